@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the compressed H-matrix-vector product y += A~ x on GB300.
+
+Workload (stand-in for the paper's Laplace single layer potential on the sphere, Section 5.1):
+n = 262144 Fibonacci points on the unit sphere, kernel 1/(4 pi |x-y|) off the diagonal and the
+mean off-diagonal row sum on it, bounding-box cluster tree with leaf size 64, standard
+admissibility with eta = 2, ACA + SVD recompression at eps = 1e-6, dense leaves in AFL and
+lowrank leaves in AFL-APLR; x ~ N(0,1) (seed 1). One step = one product (x permutation,
+phase 1, phase 2). The compressed matrix (~1.6 GB) is far larger than L2 (129 MB), so every
+step streams it from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch with torch.distributed.run: every rank runs an independent replica (the
+product does not shard on one node here), value = bytes of all ranks / max time over ranks.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compressed H-matvec GB/s & % HBM peak vs plain FP64 H-matvec; p99 solve ms"
+UNIT = "GB/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=262144)
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64/plain comparison legs")
+    return ap.parse_args()
+
+
+def workload_config(args, world: int) -> dict:
+    return {"workload": f"laplace-sphere n={args.n} eps={args.eps:g} AFL-APLR, FP32 in-block / FP64 cross-block",
+            "n": args.n, "eps": args.eps, "kernel": "1/(4 pi r), diag = mean row sum", "points": "fibonacci sphere",
+            "leaf_size": 64, "eta": 2.0, "lowrank": "ACA + SVD recompression", "rhs": 1,
+            "l2": "inputs larger than L2 (compressed matrix ~1.6 GB >> 129 MB)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
+# ------------------------------------------------------------------------------------------
+# distributed helpers (also exercised by a 2-rank gloo test on CPU)
+# ------------------------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(elapsed_s: float, units: float, world: int):
+    """(max elapsed over ranks, sum of units over ranks); a no-op for one process."""
+    if world <= 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([elapsed_s], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hlr_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def recorded_traffic(kernel: str) -> dict | None:
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel source (matched by the source hash recorded beside it)."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, "paper_2308_10960_gb300", "csrc", "hlr_kernels.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    e = d.get(kernel)
+    if not e or e.get("source_sha256_16") != h:
+        return None
+    return e
+
+
+# ------------------------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_sample(n_sample: int = 4096, eps: float = 1e-6):
+    import synth
+    from oracle import hmatrix as ohm
+    p = synth.laplace_problem(n_sample)
+    H = ohm.build_hmatrix(p, eps, method="aca")
+    C = ohm.compress(H)
+    x = synth.rhs(n_sample, 1)
+    return C, x
+
+
+def _block_bytes(b) -> int:
+    from oracle import afl
+    return sum(afl.stream_bytes(u) + 16 for u in b.units) + 8 * b.rank
+
+
+def oracle_rate(C, x, budget_s: float, min_blocks: int = 1):
+    """Time the oracle's product over whole passes (or a budget-bounded prefix of blocks)."""
+    from oracle import matvec as omv
+    from oracle import hmatrix as ohm
+    nb = len(C.blocks)
+    done_bytes = 0
+    t0 = time.perf_counter()
+    passes = 0
+    while True:
+        for i, (row0, c) in enumerate(omv.block_contributions(C, x)):
+            done_bytes += _block_bytes(C.blocks[i])
+            if time.perf_counter() - t0 > budget_s and i + 1 >= min_blocks:
+                break
+        else:
+            done_bytes += 32 * C.n
+            passes += 1
+            if time.perf_counter() - t0 < budget_s:
+                continue
+        break
+    dt = time.perf_counter() - t0
+    return done_bytes / dt / 1e9, dt, passes, done_bytes
+
+
+def cpu_baseline(args) -> dict:
+    C, x = oracle_sample(4096, args.eps)
+    gbs, dt, passes, nbytes = oracle_rate(C, x, budget_s=12.0)
+    return {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle product (AFL-APLR decode + exactly rounded FP64 sums, numpy, 1 thread) on the same "
+                      f"problem family at n=4096 (Fibonacci sphere, 1/(4 pi r), eps={args.eps:g}); "
+                      f"{passes} full passes + prefix in {dt:.1f} s, {nbytes} algorithmic bytes"}
+
+
+def run_reference(args, world: int, rank: int):
+    if rank != 0:
+        return
+    C, x = oracle_sample(4096, args.eps)
+    from oracle import matvec as omv
+    blocks = C.blocks
+    nb = len(blocks)
+    # size a step so that warmup + steps fit in ~90 s
+    t0 = time.perf_counter()
+    probe = 0
+    for i, _ in enumerate(omv.block_contributions(C, x)):
+        probe += 1
+        if time.perf_counter() - t0 > 1.0:
+            break
+    per_block = (time.perf_counter() - t0) / probe
+    per_step = max(1, min(nb, int(90.0 / max(1, args.steps + args.warmup) / per_block)))
+    gen = iter(())
+    pos = 0
+
+    def step():
+        nonlocal gen, pos
+        bytes_ = 0
+        for _ in range(per_step):
+            try:
+                row0, c = next(gen)
+            except StopIteration:
+                gen = omv.block_contributions(C, x)
+                pos = 0
+                row0, c = next(gen)
+            bytes_ += _block_bytes(blocks[pos])
+            pos += 1
+        return bytes_
+
+    for _ in range(args.warmup):
+        step()
+    total = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        total += step()
+    dt = time.perf_counter() - t0
+    v = total / dt / 1e9
+    sample = (f"oracle product on the same problem family at n=4096 (Fibonacci sphere, 1/(4 pi r), "
+              f"eps={args.eps:g}); each step = {per_step} consecutive blocks of the product, numpy, 1 thread")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def time_loop(fn, steps: int, stream):
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def run_ours(args, world: int, rank: int, local: int):
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    t_setup = time.perf_counter()
+    prob = synth.laplace_problem(args.n)
+    Hh = hg.build_kernel_hmatrix(prob.points, "laplace", args.eps, diag=prob.params["diag"], eta=2.0, leaf_size=64)
+    t_build = time.perf_counter() - t_setup
+    A = Hh.upload("afl")
+    info = A.info
+    x = torch.from_numpy(synth.rhs(args.n, 1)).to(dev)
+    y = torch.zeros(args.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    bytes_step = float(info["algorithmic_bytes"])
+
+    def step32():
+        A.matvec(x, y, acc="fp32", stream=stream, profile=True)
+
+    for _ in range(args.warmup):
+        A.matvec(x, y, acc="fp32", stream=stream)
+    torch.cuda.synchronize()
+    A.profile_read()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    el = time_loop(step32, args.steps, stream)
+    barrier(world)
+    clk = clocks.stop()
+    kms, calls = A.profile_read()
+    el_max, total_bytes = aggregate(el, bytes_step * args.steps, world)
+    value = total_bytes / el_max / 1e9
+    ms_step = el_max / args.steps * 1e3
+
+    # per-kernel roofline (dominant kernel by time)
+    peaks = measured_peaks()
+    k_names = ["k_permute", "k_phase1<AFL32>", "k_phase2<AFL32>"]
+    k_bytes = [16.0 * args.n, float(info["phase1_bytes"]), float(info["phase2_bytes"])]
+    share = [m / max(sum(kms), 1e-12) for m in kms]
+    dom = int(np.argmax(kms))
+    avg_ms = kms[dom] / max(calls, 1)
+    achieved = k_bytes[dom] / (avg_ms / 1e3) / 1e9
+    tr = recorded_traffic(k_names[dom])
+    roofline = {"bound": "hbm", "kernel": k_names[dom], "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "peak_source": f"{peaks['source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": k_bytes[dom],
+                "kernel_ms_avg": {k: m / max(calls, 1) for k, m in zip(k_names, kms)},
+                "kernel_share": dict(zip(k_names, share))}
+
+    extra = {}
+    if not args.quick:
+        steps_cmp = max(50, args.steps // 4)
+
+        def step64():
+            A.matvec(x, y, acc="fp64", stream=stream)
+        el64 = time_loop(step64, steps_cmp, stream)
+        Ap = Hh.upload("fp64")
+        infp = Ap.info
+
+        def stepp():
+            Ap.matvec(x, y, acc="fp64", stream=stream)
+        for _ in range(3):
+            stepp()
+        elp = time_loop(stepp, steps_cmp, stream)
+        t32 = el / args.steps
+        t64 = el64 / steps_cmp
+        tp = elp / steps_cmp
+        extra = {
+            "afl_fp64_acc": {"ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9},
+            "plain_fp64": {"ms_per_step": tp * 1e3, "GB/s": infp["algorithmic_bytes"] / tp / 1e9,
+                           "algorithmic_bytes": infp["algorithmic_bytes"],
+                           "pct_hbm": infp["algorithmic_bytes"] / tp / 1e9 / peaks["hbm_gbs"]},
+            "speedup_vs_plain_fp64": tp / t32,
+            "speedup_fp64acc_vs_plain_fp64": tp / t64,
+        }
+        Ap.free()
+
+    # end to end through the C-ABI call with host buffers
+    xh = torch.from_numpy(synth.rhs(args.n, 1)).pin_memory()
+    yh = torch.zeros(args.n, dtype=torch.float64).pin_memory()
+    for _ in range(3):
+        A.matvec_host(xh, yh, acc="fp32", stream=stream)
+    steps_e2e = max(50, args.steps // 4)
+    t0 = time.perf_counter()
+    for _ in range(steps_e2e):
+        A.matvec_host(xh, yh, acc="fp32", stream=stream)
+    te = (time.perf_counter() - t0) / steps_e2e
+    te_max, _ = aggregate(te, 0.0, world)
+    e2e = {"value": world * bytes_step / te_max / 1e9, "unit": UNIT, "h2d_bytes_per_step": 16 * args.n,
+           "d2h_bytes_per_step": 8 * args.n, "ms_per_step": te_max * 1e3,
+           "api": "hlr_matvec_host (pinned host x, y; copies inside the timed region)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, world),
+               "pct_hbm_peak": value / world / peaks["hbm_gbs"], "pct_hbm_8tbs_spec": value / world / 8000.0,
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+               "gpu_launches": 3 * args.steps,
+               "matrix": {"nblocks": info["nblocks"], "rank_sum": info["rank_sum"],
+                          "compressed_bytes": info["stream_bytes"] + info["header_bytes"] + 8 * info["rank_sum"],
+                          "fp64_bytes": info["fp64_bytes"],
+                          "ratio": (info["stream_bytes"] + info["header_bytes"] + 8 * info["rank_sum"]) /
+                                   info["fp64_bytes"],
+                          "algorithmic_bytes_per_step": bytes_step, "build_s": t_build},
+               **extra}
+        print(json.dumps(out), flush=True)
+    A.free()
+    Hh.free()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            if rank != 0:
+                return
+        else:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

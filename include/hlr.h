@@ -1,0 +1,207 @@
+/*
+ * hlr.h -- C ABI of the GB300 compressed H-matrix library.
+ *
+ * The library stores an H-matrix (Def. 2.3: a block partition of I x I whose admissible leaves
+ * are lowrank and whose other leaves are dense, with eps-accurate lowrank leaves as in Eq. 1)
+ * in the AFL binary compression of Section 3.2, every lowrank factor column at its own
+ * precision (APLR, Section 3.3), and applies it to vectors on one GPU (Section 5.4), decoding
+ * the bit streams inside the product kernels.
+ *
+ * Conventions for every call
+ *  - All functions return HLR_OK (0) on success and a negative HLR_ERR_* code otherwise; the
+ *    calling thread's message is then available from hlr_last_error(). No C++ exception
+ *    crosses this boundary.
+ *  - "_dev" pointers are device pointers of the current CUDA device; other pointers are host
+ *    pointers. The caller keeps ownership of every buffer it passes.
+ *  - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream unless stated otherwise.
+ *  - Vectors are FP64 in ORIGINAL index order; the cluster permutation is applied inside.
+ *  - A handle may be used from several threads for read-only calls; calls that overlap on the
+ *    GPU with the same handle and different streams race on the handle's scratch memory and
+ *    must be serialised by the caller.
+ */
+#ifndef HLR_H
+#define HLR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define HLR_OK               0
+#define HLR_ERR_INVALID     (-1)  /* bad argument, shape, coverage, NaN/Inf, unknown handle   */
+#define HLR_ERR_OOM         (-2)  /* device or pinned host allocation failed                 */
+#define HLR_ERR_CUDA        (-3)  /* a CUDA runtime call or kernel launch failed             */
+#define HLR_ERR_TIMEOUT     (-4)  /* a bounded device-side wait expired                      */
+#define HLR_ERR_NOCONV      (-5)  /* CG reached maxit; x holds the last iterate              */
+#define HLR_ERR_UNSUPPORTED (-6)  /* valid request outside this build's limits               */
+
+/* ---- block kinds and storage formats ---------------------------------------------------- */
+#define HLR_DENSE   0
+#define HLR_LOWRANK 1
+
+#define HLR_FMT_AFL_APLR 1  /* dense leaves: one AFL unit at eps; lowrank: AFL-APLR columns  */
+#define HLR_FMT_FP64     2  /* plain uncompressed FP64 factors (the baseline H-matvec)        */
+
+/* ---- product flags ---------------------------------------------------------------------- */
+#define HLR_ACC_FP64 0  /* decode to FP64 and accumulate in FP64 everywhere                    */
+#define HLR_ACC_FP32 1  /* decode to FP32, FP32 sums inside a block, FP64 across blocks into y */
+#define HLR_PROFILE  0x100 /* OR-ed into flags: record CUDA events around each kernel launch of the
+                              product on cuda_stream, for hlr_profile_read (adds no synchronisation) */
+
+typedef uint64_t hlr_handle; /* 0 is never a valid handle */
+
+/* One leaf block b = (tau, sigma) of the block tree (Def. 2.2) in CLUSTER order: rows
+ * [row0, row0+nrows) and columns [col0, col0+ncols) are positions of the permutation perm.
+ *  dense  : D, nrows x ncols, column-major.
+ *  lowrank: W (nrows x rank) and X (ncols x rank) column-major with orthonormal columns and
+ *           sigma[rank] > 0 descending, so that the block is W diag(sigma) X^T (Section 3.3).
+ * Unused pointers may be NULL. */
+typedef struct {
+  int64_t row0, nrows, col0, ncols;
+  int32_t kind;
+  int32_t rank;
+  const double *D;
+  const double *W;
+  const double *sigma;
+  const double *X;
+} hlr_block_desc;
+
+/* A whole H-matrix. perm[p] is the original index of cluster position p (NULL = identity).
+ * The leaves must cover {0..n-1} x {0..n-1} exactly once. eps is the accuracy of Eq. 1; it
+ * sets the precision of every AFL unit (dense: eps; lowrank column i: eps sigma_0 / sigma_i). */
+typedef struct {
+  int64_t n;
+  const int64_t *perm;
+  int64_t nblocks;
+  const hlr_block_desc *blocks;
+  double eps;
+  int32_t format;   /* HLR_FMT_AFL_APLR or HLR_FMT_FP64 */
+  int32_t reserved; /* must be 0 */
+} hlr_hmatrix_desc;
+
+/* Sizes of an uploaded matrix (hlr_get_info). Byte counts exclude alignment padding. */
+typedef struct {
+  int64_t n, nblocks, ndense, nlowrank, nunits, nleaves, nitems;
+  int64_t rank_sum, values;
+  uint64_t fp64_bytes;        /* 8 per stored value + 8 per singular value                  */
+  uint64_t stream_bytes;      /* compressed (or FP64) factor bytes, unpadded                */
+  uint64_t header_bytes;      /* 16 per unit (m_min, offset, e, m, width)                    */
+  uint64_t algorithmic_bytes; /* bytes one y += A x must move: streams + headers + 8 per
+                                 singular value + 8n (x) + 16n (y read and write) + 8n (perm) */
+  uint64_t device_bytes;      /* size of the device arena                                   */
+  double flops;               /* 2 k (#tau + #sigma) per lowrank + 2 #tau #sigma per dense  */
+  uint64_t phase1_bytes;      /* phase 1 (t = Sigma X~^T x): X streams + X headers + 16 per
+                                 singular value (Sigma read, t written) + 4n (x, once)        */
+  uint64_t phase2_bytes;      /* phase 2: W and dense streams + their headers + 8 per singular
+                                 value (t) + 8n (x, once) + 16n (y) + 8n (perm)              */
+} hlr_info;
+
+/* Encode the matrix (AFL-APLR or FP64), build the work lists of the product (blocks grouped by
+ * leaf row cluster) and copy everything to one device arena. Synchronous: returns after the
+ * copy has completed on cuda_stream. The caller may free the descriptor on return.
+ * Errors: HLR_ERR_INVALID (shape, coverage, perm, NaN/Inf, rank/sigma), HLR_ERR_OOM,
+ * HLR_ERR_CUDA, HLR_ERR_UNSUPPORTED (arena > 16 TiB). Section 3, Section 3.3. */
+int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_handle *out, size_t *device_bytes);
+
+/* y_dev += A~ x_dev (Section 5.4) where A~ is the decoded stored matrix; x_dev and y_dev hold
+ * n FP64 values in original order and must not overlap. flags: HLR_ACC_FP64 or HLR_ACC_FP32
+ * (ignored for HLR_FMT_FP64, which always computes in FP64). Deterministic: the same inputs
+ * give the same bits. Errors: HLR_ERR_INVALID, HLR_ERR_CUDA. */
+int hlr_matvec(hlr_handle h, const double *x_dev, double *y_dev, int flags, void *cuda_stream);
+
+/* y_host += A~ x_host with HOST buffers (n FP64 values each, original order): copies x and y to
+ * the handle's device buffers on cuda_stream, computes the product there and copies y back, then
+ * waits for the stream. Pinned host memory makes the copies asynchronous DMA. Same flags and
+ * errors as hlr_matvec. */
+int hlr_matvec_host(hlr_handle h, const double *x_host, double *y_host, int flags, void *cuda_stream);
+
+/* Many products in one launch sequence: for request q, Y_q += A~_q X_q with X_q, Y_q holding
+ * nrhs[q] columns (leading dimensions ldx[q], ldy[q] >= n_q, column-major). The pointer
+ * arrays are host arrays of device pointers. Requests may repeat a handle only if their Y
+ * blocks do not overlap. Errors: HLR_ERR_INVALID, HLR_ERR_OOM, HLR_ERR_CUDA. */
+int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
+                       const double *const *X_dev, const int64_t *ldx,
+                       double *const *Y_dev, const int64_t *ldy, int flags, void *cuda_stream);
+
+/* Unpreconditioned conjugate gradients for A~ x = b (A~ symmetric positive definite), with
+ * x_dev as initial guess on entry and the solution on return. Stops when the recursive
+ * residual satisfies ||r|| <= rtol ||b||. Inner products and vector updates are FP64;
+ * the products use flags. Synchronous (returns *iters and *relres, the relative TRUE
+ * residual ||b - A~ x|| / ||b|| of the returned x). HLR_ERR_NOCONV when maxit is reached. */
+int hlr_solve_cg(hlr_handle h, const double *b_dev, double *x_dev, double rtol, int maxit,
+                 int flags, void *cuda_stream, int *iters, double *relres);
+
+/* Release the device arena of h (synchronises the device first). */
+int hlr_free(hlr_handle h);
+
+/* Message of the calling thread's most recent failure ("" if none). Never NULL. */
+const char *hlr_last_error(void);
+
+/* Fill *out with the sizes of an uploaded matrix. */
+int hlr_get_info(hlr_handle h, hlr_info *out);
+
+/* Per-kernel device time of the products launched with HLR_PROFILE since the previous read:
+ * kernel_ms[0] = x permutation, [1] = phase 1 (t = Sigma X~^T x), [2] = phase 2 (y += W~ t, D~ x),
+ * summed over *calls products. Waits for the recorded events. At most 4096 products are kept
+ * between reads; later ones are not recorded. */
+int hlr_profile_read(hlr_handle h, double *kernel_ms, int *calls);
+
+/* ---- codec entry points ----------------------------------------------------------------- */
+
+/* AFL-encode n FP64 values (one unit, Section 3.2) at precision u on the HOST (no GPU needed).
+ * Writes m_min, e, m and the packed stream (value j at bits [j w, (j+1) w), w = 1+e+m,
+ * LSB-first, zero-padded to a multiple of 16 bytes) into out[cap]; *nbytes = padded size.
+ * HLR_ERR_INVALID for NaN/Inf input or u <= 0; HLR_ERR_OOM if cap is too small. */
+int hlr_afl_encode(const double *a, int64_t n, double u, double *m_min, int32_t *e, int32_t *m,
+                   uint8_t *out, size_t cap, size_t *nbytes);
+
+/* Decode one AFL stream on the GPU into n FP64 values, bit-exact IEEE round-to-nearest
+ * ((v - 1) * m_min without contraction, Section 3.2). stream_dev must be 16-byte aligned and
+ * hold ceil(n (1+e+m) / 8) bytes rounded up to 16. */
+int hlr_afl_decode_device(const uint8_t *stream_dev, int64_t n, double m_min, int32_t e, int32_t m,
+                          double *out_dev, void *cuda_stream);
+
+/* Decode every unit of an uploaded matrix to FP64 on the GPU, concatenated in unit order
+ * (per block in block order: dense -> its column-major values; lowrank -> W columns then X
+ * columns). cap is the capacity of out_dev in doubles (>= hlr_info.values). */
+int hlr_decode_units(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stream);
+
+/* ---- construction of kernel matrices (host, multithreaded) --------------------------------- */
+#define HLR_KERNEL_EXP      1  /* exp(-|x-y| / scale) + diag * [i == j]                           */
+#define HLR_KERNEL_LAPLACE  2  /* 1 / (4 pi |x-y|) for i != j, diag for i == j                     */
+#define HLR_KERNEL_MATERN15 3  /* (1 + sqrt3 |x-y|/scale) exp(-sqrt3 |x-y|/scale) + diag [i == j]  */
+
+typedef struct {
+  int32_t kernel;
+  int32_t dim;           /* 1..3 */
+  int64_t n;
+  const double *points;  /* n x dim, row-major */
+  double scale;
+  double diag;
+  double eps;            /* Eq. 1 accuracy of the lowrank leaves */
+  double eta;            /* standard admissibility parameter (Section 5.1) */
+  int32_t leaf_size;
+  int32_t threads;       /* 0 = all */
+} hlr_kernel_problem;
+
+typedef struct hlr_host_hmatrix hlr_host_hmatrix; /* opaque, owned by the library */
+
+/* Build the FP64 H-matrix of a kernel problem: bounding-box bisection cluster tree (Def. 2.1),
+ * block tree with standard admissibility (Def. 2.2), dense leaves evaluated, admissible
+ * leaves by ACA with partial pivoting at eps/10 followed by SVD recompression (Algorithm 1)
+ * truncated at sigma_i > eps sigma_0. Errors: HLR_ERR_INVALID, HLR_ERR_OOM. */
+int hlr_build(const hlr_kernel_problem *p, hlr_host_hmatrix **out);
+
+/* Describe a built matrix: fills *d with pointers into hm (valid until hlr_host_free). */
+int hlr_host_describe(const hlr_host_hmatrix *hm, hlr_hmatrix_desc *d);
+
+void hlr_host_free(hlr_host_hmatrix *hm);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HLR_H */

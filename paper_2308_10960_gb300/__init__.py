@@ -1,0 +1,294 @@
+"""GB300-native compressed H-matrix-vector product (Kriemann, "Hierarchical Lowrank Arithmetic
+with Binary Compression", arXiv 2308.10960).
+
+Python face of the C ABI in ``include/hlr.h``. An H-matrix (Def. 2.3) is uploaded once; its
+dense leaves are stored in the AFL binary format and its lowrank leaves W Sigma X^T column by
+column at adaptive precision (AFL-APLR, Sections 3.2-3.3). ``DeviceHMatrix.matvec`` computes
+y += A~ x (Section 5.4) in hand-written sm_103a kernels that decode the bit streams on the fly.
+PyTorch provides device memory and streams only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _binding as B
+from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ERR_INVALID, HLR_ERR_NOCONV, HLR_FMT_AFL_APLR,
+                       HLR_FMT_FP64, HLR_KERNEL_EXP, HLR_KERNEL_LAPLACE, HLR_KERNEL_MATERN15, HLR_LOWRANK, HlrError)
+
+__all__ = [
+    "HlrError", "DeviceHMatrix", "HostHMatrix", "upload", "build_kernel_hmatrix", "afl_encode",
+    "afl_decode_device", "matvec_batched", "HLR_ACC_FP32", "HLR_ACC_FP64", "HLR_FMT_AFL_APLR", "HLR_FMT_FP64",
+    "HLR_DENSE", "HLR_LOWRANK", "lib_path",
+]
+
+_ACC = {"fp32": HLR_ACC_FP32, "fp64": HLR_ACC_FP64, HLR_ACC_FP32: HLR_ACC_FP32, HLR_ACC_FP64: HLR_ACC_FP64}
+_FMT = {"afl": HLR_FMT_AFL_APLR, "fp64": HLR_FMT_FP64, HLR_FMT_AFL_APLR: HLR_FMT_AFL_APLR, HLR_FMT_FP64: HLR_FMT_FP64}
+_KERNEL = {"exp2d": HLR_KERNEL_EXP, "exp": HLR_KERNEL_EXP, "laplace": HLR_KERNEL_LAPLACE,
+           "matern15": HLR_KERNEL_MATERN15}
+
+
+def lib_path() -> str:
+    return B.LIB_PATH
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            return None          # legacy default stream; host-only calls fail before using it
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, n: int | None = None) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise HlrError(HLR_ERR_INVALID, "expected a contiguous float64 CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise HlrError(HLR_ERR_INVALID, f"tensor has {t.numel()} elements, need {n}")
+    return t.data_ptr()
+
+
+def _host_ptr(a, n: int) -> int:
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size < n:
+            raise HlrError(HLR_ERR_INVALID, "expected a contiguous float64 host array")
+        return a.ctypes.data
+    import torch
+    if not isinstance(a, torch.Tensor) or a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous() \
+            or a.numel() < n:
+        raise HlrError(HLR_ERR_INVALID, "expected a contiguous float64 host tensor")
+    return a.data_ptr()
+
+
+class _DescBuilder:
+    """Holds the ctypes descriptor and keeps every referenced numpy array alive."""
+
+    def __init__(self, n: int, perm, blocks, eps: float, fmt: int):
+        self.keep = []
+        self.n = int(n)
+        self.perm = None if perm is None else np.ascontiguousarray(perm, dtype=np.int64)
+        arr = (B.BlockDesc * len(blocks))()
+        for i, b in enumerate(blocks):
+            d = arr[i]
+            d.row0, d.nrows, d.col0, d.ncols = int(b["row0"]), int(b["nrows"]), int(b["col0"]), int(b["ncols"])
+            d.kind = int(b["kind"])
+            if d.kind == HLR_DENSE:
+                D = np.asfortranarray(b["D"], dtype=np.float64)
+                self.keep.append(D)
+                d.D = B.f64ptr(D)
+                d.rank = 0
+            else:
+                S = np.ascontiguousarray(b["S"], dtype=np.float64)
+                d.rank = int(S.size)
+                if S.size:
+                    W = np.asfortranarray(b["W"], dtype=np.float64)
+                    X = np.asfortranarray(b["X"], dtype=np.float64)
+                    self.keep += [W, X, S]
+                    d.W, d.X, d.sigma = B.f64ptr(W), B.f64ptr(X), B.f64ptr(S)
+        self.arr = arr
+        self.desc = B.HMatrixDesc()
+        self.desc.n = self.n
+        self.desc.perm = None if self.perm is None else self.perm.ctypes.data_as(B._i64p)
+        self.desc.nblocks = len(blocks)
+        self.desc.blocks = C.cast(arr, C.POINTER(B.BlockDesc))
+        self.desc.eps = float(eps)
+        self.desc.format = fmt
+        self.desc.reserved = 0
+
+
+class DeviceHMatrix:
+    """An uploaded compressed H-matrix (owns a library handle)."""
+
+    def __init__(self, handle: int):
+        self.handle = int(handle)
+        inf = B.Info()
+        B.check(B.lib.hlr_get_info(C.c_uint64(self.handle), C.byref(inf)))
+        self.info = inf.as_dict()
+        self.n = int(self.info["n"])
+
+    def matvec(self, x, y, acc="fp32", stream=None, profile=False):
+        """y += A~ x (both contiguous float64 CUDA tensors of length n, original order)."""
+        flags = _ACC[acc] | (B.HLR_PROFILE if profile else 0)
+        B.check(B.lib.hlr_matvec(C.c_uint64(self.handle), _dev_ptr(x, self.n), _dev_ptr(y, self.n),
+                                 flags, _stream_ptr(stream)))
+        return y
+
+    def profile_read(self):
+        """(per-kernel milliseconds [permute, phase1, phase2] summed, number of products) of the
+        products launched with profile=True since the previous read."""
+        ms = (C.c_double * 3)()
+        calls = C.c_int(0)
+        B.check(B.lib.hlr_profile_read(C.c_uint64(self.handle), ms, C.byref(calls)))
+        return list(ms), calls.value
+
+    def matvec_host(self, x, y, acc="fp32", stream=None):
+        """y += A~ x with HOST buffers (numpy arrays or CPU tensors, pinned for async copies):
+        copies in, computes on the GPU, copies y back and waits (hlr_matvec_host)."""
+        xp = _host_ptr(x, self.n)
+        yp = _host_ptr(y, self.n)
+        B.check(B.lib.hlr_matvec_host(C.c_uint64(self.handle), xp, yp, _ACC[acc], _stream_ptr(stream)))
+        return y
+
+    def solve_cg(self, b, x, rtol=1e-8, maxit=1000, acc="fp64", stream=None, raise_noconv=True):
+        """Solve A~ x = b by CG (x holds the initial guess). Returns (iterations, true rel. residual)."""
+        it = C.c_int(0)
+        rel = C.c_double(0.0)
+        rc = B.lib.hlr_solve_cg(C.c_uint64(self.handle), _dev_ptr(b, self.n), _dev_ptr(x, self.n), float(rtol),
+                                int(maxit), _ACC[acc], _stream_ptr(stream), C.byref(it), C.byref(rel))
+        if rc == HLR_ERR_NOCONV and not raise_noconv:
+            return it.value, rel.value
+        B.check(rc)
+        return it.value, rel.value
+
+    def decode_units(self, out):
+        """Decode every stored unit to FP64 on the GPU (bit-exact path), concatenated in unit order."""
+        B.check(B.lib.hlr_decode_units(C.c_uint64(self.handle), _dev_ptr(out), out.numel(), _stream_ptr(None)))
+        return out
+
+    def free(self):
+        if self.handle:
+            B.check(B.lib.hlr_free(C.c_uint64(self.handle)))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            if self.handle:
+                B.lib.hlr_free(C.c_uint64(self.handle))
+        except Exception:
+            pass
+
+
+def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None) -> DeviceHMatrix:
+    """Upload an H-matrix given as a list of block dicts (row0, nrows, col0, ncols, kind and D
+    or W, S, X as numpy arrays, cluster order) with perm[p] = original index of position p."""
+    db = _DescBuilder(n, perm, blocks, eps, _FMT[fmt])
+    h = C.c_uint64(0)
+    nbytes = C.c_size_t(0)
+    B.check(B.lib.hlr_upload(C.byref(db.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))
+    return DeviceHMatrix(h.value)
+
+
+def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None):
+    """Y_q += A~_q X_q for every request q (X_q, Y_q: n_q x r_q column-major float64 CUDA tensors,
+    i.e. tensors of shape (r_q, n_q) in row-major memory, or 1-D of length n_q)."""
+    q = len(mats)
+    hs = (C.c_uint64 * q)(*[m.handle for m in mats])
+    nr = (C.c_int32 * q)()
+    xp = (C.c_void_p * q)()
+    yp = (C.c_void_p * q)()
+    lx = (C.c_int64 * q)()
+    ly = (C.c_int64 * q)()
+    for i, (m, X, Y) in enumerate(zip(mats, Xs, Ys)):
+        r = 1 if X.dim() == 1 else X.shape[0]
+        nr[i] = r
+        xp[i] = _dev_ptr(X, m.n * r)
+        yp[i] = _dev_ptr(Y, m.n * r)
+        lx[i] = m.n
+        ly[i] = m.n
+    B.check(B.lib.hlr_matvec_batched(q, hs, nr, xp, lx, yp, ly, _ACC[acc], _stream_ptr(stream)))
+
+
+class HostHMatrix:
+    """An FP64 H-matrix built on the host by the library (owns a host object)."""
+
+    def __init__(self, ptr: int, points: np.ndarray):
+        self.ptr = ptr
+        self._points = points
+        self.desc = B.HMatrixDesc()
+        B.check(B.lib.hlr_host_describe(C.c_void_p(self.ptr), C.byref(self.desc)))
+        self.n = int(self.desc.n)
+        self.eps = float(self.desc.eps)
+
+    @property
+    def perm(self) -> np.ndarray:
+        return np.ctypeslib.as_array(self.desc.perm, shape=(self.n,)).copy()
+
+    def structure(self) -> np.ndarray:
+        """(nblocks, 6) int64 array: row0, nrows, col0, ncols, kind, rank."""
+        out = np.zeros((self.desc.nblocks, 6), dtype=np.int64)
+        for i in range(self.desc.nblocks):
+            d = self.desc.blocks[i]
+            out[i] = (d.row0, d.nrows, d.col0, d.ncols, d.kind, d.rank)
+        return out
+
+    def block(self, i: int) -> dict:
+        """Copy of block i as numpy arrays (D, or W, S, X)."""
+        d = self.desc.blocks[i]
+        b = {"row0": d.row0, "nrows": d.nrows, "col0": d.col0, "ncols": d.ncols, "kind": d.kind}
+        if d.kind == HLR_DENSE:
+            b["D"] = np.ctypeslib.as_array(d.D, shape=(d.nrows * d.ncols,)).reshape(d.nrows, d.ncols, order="F").copy()
+        else:
+            k = d.rank
+            b["S"] = np.ctypeslib.as_array(d.sigma, shape=(k,)).copy() if k else np.zeros(0)
+            b["W"] = np.ctypeslib.as_array(d.W, shape=(d.nrows * k,)).reshape(d.nrows, k, order="F").copy() \
+                if k else np.zeros((d.nrows, 0))
+            b["X"] = np.ctypeslib.as_array(d.X, shape=(d.ncols * k,)).reshape(d.ncols, k, order="F").copy() \
+                if k else np.zeros((d.ncols, 0))
+        return b
+
+    def upload(self, fmt="afl", eps: float | None = None, stream=None) -> DeviceHMatrix:
+        """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU."""
+        self.desc.format = _FMT[fmt]
+        self.desc.eps = self.eps if eps is None else float(eps)
+        h = C.c_uint64(0)
+        nbytes = C.c_size_t(0)
+        B.check(B.lib.hlr_upload(C.byref(self.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))
+        return DeviceHMatrix(h.value)
+
+    def free(self):
+        if self.ptr:
+            B.lib.hlr_host_free(C.c_void_p(self.ptr))
+            self.ptr = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_kernel_hmatrix(points: np.ndarray, kernel: str, eps: float, scale: float = 1.0, diag: float = 0.0,
+                         eta: float = 2.0, leaf_size: int = 64, threads: int = 0) -> HostHMatrix:
+    """Build the FP64 H-matrix of a kernel matrix on the host (cluster tree, block tree, ACA +
+    SVD recompression), multithreaded in native code."""
+    P = np.ascontiguousarray(points, dtype=np.float64)
+    prob = B.KernelProblem()
+    prob.kernel = _KERNEL[kernel]
+    prob.dim = P.shape[1]
+    prob.n = P.shape[0]
+    prob.points = B.f64ptr(P)
+    prob.scale = float(scale)
+    prob.diag = float(diag)
+    prob.eps = float(eps)
+    prob.eta = float(eta)
+    prob.leaf_size = int(leaf_size)
+    prob.threads = int(threads)
+    out = C.c_void_p(0)
+    B.check(B.lib.hlr_build(C.byref(prob), C.byref(out)))
+    return HostHMatrix(out.value, P)
+
+
+def afl_encode(a: np.ndarray, u: float):
+    """Host AFL encoder of the library: returns (m_min, e, m, stream bytes padded to 16)."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    m_min = C.c_double(0)
+    e = C.c_int32(0)
+    m = C.c_int32(0)
+    nbytes = C.c_size_t(0)
+    cap = (a.size * 64 + 7) // 8 + 32
+    buf = np.zeros(cap, dtype=np.uint8)
+    B.check(B.lib.hlr_afl_encode(B.f64ptr(a), a.size, float(u), C.byref(m_min), C.byref(e), C.byref(m),
+                                 buf.ctypes.data_as(C.c_void_p), cap, C.byref(nbytes)))
+    return m_min.value, e.value, m.value, buf[: nbytes.value].tobytes()
+
+
+def afl_decode_device(stream_dev, n: int, m_min: float, e: int, m: int, out, stream=None):
+    """Decode one AFL stream (uint8 CUDA tensor, 16-byte aligned) into out (float64 CUDA tensor)."""
+    B.check(B.lib.hlr_afl_decode_device(stream_dev.data_ptr(), int(n), float(m_min), int(e), int(m),
+                                        _dev_ptr(out, n), _stream_ptr(stream)))
+    return out

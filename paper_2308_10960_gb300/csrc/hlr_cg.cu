@@ -1,0 +1,205 @@
+// hlr_solve_cg: unpreconditioned conjugate gradients on the compressed operator, with FP64
+// vectors, FP64 inner products reduced in a fixed order (deterministic), and the products
+// computed by the compressed H-matrix-vector kernels (Section 5.4).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "hlr_internal.h"
+
+namespace hlr {
+namespace {
+
+constexpr int kDotBlocks = 608;   // fixed grid of the reductions: 4 x 152 SMs (order is fixed)
+constexpr int kDotThreads = 256;
+
+enum { S_RR = 0, S_PAP = 1, S_RRNEW = 2, S_BB = 3, S_TMP = 4, S_N = 8 };
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kDotThreads / 32; ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+// partial[b] = sum over the block's grid-stride share of a[i] * b[i]
+__global__ void k_dot(const double *__restrict__ a, const double *__restrict__ b, int64_t n, double *partial) {
+  __shared__ double sh[kDotThreads / 32];
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(kDotThreads) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * kDotThreads)
+    v = fma(a[i], b[i], v);
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_dot_final(const double *partial, double *out) {
+  __shared__ double sh[kDotThreads / 32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < kDotBlocks; i += kDotThreads) v += partial[i];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// r = b - Ap ; p = r ; Ap = 0
+__global__ void k_init(const double *__restrict__ b, double *__restrict__ r, double *__restrict__ p,
+                       double *__restrict__ Ap, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const double v = b[i] - Ap[i];
+    r[i] = v;
+    p[i] = v;
+    Ap[i] = 0.0;
+  }
+}
+
+// alpha = rr / pAp ; x += alpha p ; r -= alpha Ap ; partial of r.r
+__global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                            const double *__restrict__ Ap, const double *scal, int64_t n, double *partial) {
+  __shared__ double sh[kDotThreads / 32];
+  const double alpha = scal[S_RR] / scal[S_PAP];
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(kDotThreads) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * kDotThreads) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    v = fma(ri, ri, v);
+  }
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// beta = rrnew / rr ; p = r + beta p ; Ap = 0 ; rr = rrnew
+__global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, double *__restrict__ Ap,
+                           double *scal, int64_t n) {
+  const double beta = scal[S_RRNEW] / scal[S_RR];
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    p[i] = fma(beta, p[i], r[i]);
+    Ap[i] = 0.0;
+  }
+}
+
+__global__ void k_copy_scalar(double *scal, int dst, int src) { scal[dst] = scal[src]; }
+
+__global__ void k_residual(const double *__restrict__ b, double *__restrict__ Ax, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    Ax[i] = b[i] - Ax[i];
+}
+
+struct CgWork {
+  double *r, *p, *Ap, *partial, *scal;
+};
+
+int ck(cudaError_t e, const char *what) {
+  if (e != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return HLR_OK;
+}
+
+}  // namespace
+
+int cg_workspace(Handle &H, void **ws) {
+  const size_t n = size_t(H.L.n);
+  const size_t bytes = 8 * (3 * n + kDotBlocks + S_N) + 1024;
+  if (!H.cg_ws) {
+    if (cudaMalloc(&H.cg_ws, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      H.cg_ws = nullptr;
+      return set_error(HLR_ERR_OOM, "hlr_solve_cg: workspace allocation failed");
+    }
+  }
+  *ws = H.cg_ws;
+  return HLR_OK;
+}
+
+int solve_cg(Handle &H, const double *b, double *x, double rtol, int maxit, int flags, void *stream, int *iters,
+             double *relres) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void *ws = nullptr;
+  int rc = cg_workspace(H, &ws);
+  if (rc) return rc;
+  const int64_t n = H.L.n;
+  double *base = static_cast<double *>(ws);
+  CgWork W{base, base + n, base + 2 * n, base + 3 * n, base + 3 * n + kDotBlocks};
+  const int gv = 2 * kDotBlocks;
+  double h_scal[S_N];
+  auto dot = [&](const double *a, const double *c, int slot) {
+    k_dot<<<kDotBlocks, kDotThreads, 0, st>>>(a, c, n, W.partial);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + slot);
+  };
+  // Ap = A x ; r = b - Ap ; p = r
+  if ((rc = ck(cudaMemsetAsync(W.Ap, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
+  if ((rc = launch_matvec(H, x, W.Ap, flags, st))) return rc;
+  k_init<<<gv, 256, 0, st>>>(b, W.r, W.p, W.Ap, n);
+  dot(b, b, S_BB);
+  dot(W.r, W.r, S_RR);
+  if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
+  if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
+  const double bnorm = std::sqrt(h_scal[S_BB]);
+  double rr = h_scal[S_RR];
+  int it = 0;
+  bool conv = bnorm == 0.0 || std::sqrt(rr) <= rtol * bnorm;
+  while (!conv && it < maxit) {
+    if ((rc = launch_matvec(H, W.p, W.Ap, flags, st))) return rc;
+    dot(W.p, W.Ap, S_PAP);
+    k_update_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, W.r, W.p, W.Ap, W.scal, n, W.partial);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + S_RRNEW);
+    k_update_p<<<gv, 256, 0, st>>>(W.p, W.r, W.Ap, W.scal, n);
+    k_copy_scalar<<<1, 1, 0, st>>>(W.scal, S_RR, S_RRNEW);
+    if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
+    if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
+    rr = h_scal[S_RR];
+    ++it;
+    if (!std::isfinite(rr)) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: breakdown (non-finite residual)");
+    conv = std::sqrt(rr) <= rtol * bnorm;
+  }
+  // true residual of the returned x
+  if ((rc = ck(cudaMemsetAsync(W.Ap, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
+  if ((rc = launch_matvec(H, x, W.Ap, flags, st))) return rc;
+  k_residual<<<gv, 256, 0, st>>>(b, W.Ap, n);
+  dot(W.Ap, W.Ap, S_TMP);
+  if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
+  if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
+  if (iters) *iters = it;
+  if (relres) *relres = bnorm > 0 ? std::sqrt(h_scal[S_TMP]) / bnorm : 0.0;
+  if (!conv) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: maxit reached");
+  return HLR_OK;
+}
+
+}  // namespace hlr
+
+using namespace hlr;
+
+extern "C" int hlr_solve_cg(hlr_handle h, const double *b, double *x, double rtol, int maxit, int flags,
+                            void *stream, int *iters, double *relres) {
+  Handle *H = lookup(h);
+  if (!H) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: unknown handle");
+  if (!b || !x || !(rtol > 0) || maxit < 0) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: bad arguments");
+  if (flags != HLR_ACC_FP64 && flags != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: bad flags");
+  return solve_cg(*H, b, x, rtol, maxit, flags, stream, iters, relres);
+}
+
+extern "C" int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs, const double *const *X,
+                                  const int64_t *ldx, double *const *Y, const int64_t *ldy, int flags,
+                                  void *stream) {
+  if (nreq < 0 || (nreq > 0 && (!h || !nrhs || !X || !ldx || !Y || !ldy)))
+    return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad arguments");
+  if (flags != HLR_ACC_FP64 && flags != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad flags");
+  for (int q = 0; q < nreq; ++q) {
+    Handle *H = lookup(h[q]);
+    if (!H) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: unknown handle");
+    if (nrhs[q] < 0 || (nrhs[q] > 0 && (!X[q] || !Y[q])) || ldx[q] < H->L.n || ldy[q] < H->L.n)
+      return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad request " + std::to_string(q));
+  }
+  for (int q = 0; q < nreq; ++q) {
+    Handle *H = lookup(h[q]);
+    for (int j = 0; j < nrhs[q]; ++j) {
+      int rc = launch_matvec(*H, X[q] + ldx[q] * j, Y[q] + ldy[q] * j, flags, stream);
+      if (rc) return rc;
+    }
+  }
+  return HLR_OK;
+}

@@ -1,0 +1,56 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks aggregate their timings (max) and their
+work (sum) exactly as the GPU ranks do under torchrun."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    w, r, l = bench.dist_env()
+    el, units = bench.aggregate(0.5 + rank, 100.0 * (rank + 1), w)
+    bench.barrier(w)
+    q.put((r, w, el, units))
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregate():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 2, 1.5, 300.0), (1, 2, 1.5, 300.0)]
+
+
+def test_bench_parses_defaults():
+    import sys
+    import bench
+    old = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        a = bench.parse()
+    finally:
+        sys.argv = old
+    assert a.gpus == 1 and a.steps >= 3 and a.warmup >= 3 and a.impl == "ours"

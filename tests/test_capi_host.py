@@ -1,0 +1,133 @@
+"""Host-side tests of the native library (no GPU): the shared library loads and exports every
+symbol include/hlr.h declares; the host AFL encoder is byte-exact with the oracle encoder; the
+native construction reproduces the oracle's cluster tree, block tree and ranks and meets Eq. 1;
+upload rejects invalid descriptors before touching the GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import afl
+from oracle import hmatrix as ohm
+from tests._util import header_symbols, oracle_blocks
+
+hg = pytest.importorskip("paper_2308_10960_gb300")
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ctypes.CDLL(hg.lib_path())
+    names = header_symbols()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    from paper_2308_10960_gb300 import _binding
+    assert sorted(s[0] for s in _binding.SIGNATURES) == names
+
+
+def _enc_cases():
+    g = np.random.default_rng(21)
+    yield g.standard_normal(1)
+    yield g.standard_normal(777)
+    yield np.exp(g.uniform(-60, 60, size=333)) * g.choice([-1.0, 1.0], size=333)
+    z = g.standard_normal(129)
+    z[::3] = 0.0
+    yield z
+    yield np.zeros(17)
+    yield np.array([1.0, 2.0 - 2.0 ** -40, -(4.0 - 2.0 ** -30), 7.999999, -0.0])
+
+
+@pytest.mark.parametrize("m", list(range(0, 53, 1)))
+def test_host_encoder_byte_exact_with_oracle(m):
+    u = 1.0 if m == 0 else 2.0 ** -m * 1.3
+    for a in _enc_cases():
+        mm, e, mb, data = hg.afl_encode(a, u)
+        o = afl.encode(a, u)
+        assert (mm, e, mb) == (o.m_min, o.e, o.m)
+        assert data == o.data
+
+
+def test_host_encoder_precisions_like_aplr():
+    g = np.random.default_rng(4)
+    s = np.sort(np.exp(g.uniform(-12, 0, size=20)))[::-1]
+    for ui in afl.aplr_precisions(s, 1e-6):
+        a = g.standard_normal(64)
+        assert hg.afl_encode(a, ui)[3] == afl.encode(a, ui).data
+
+
+@pytest.mark.parametrize("name", ["exp2d", "laplace", "matern"])
+def test_native_construction_matches_oracle(name):
+    if name == "exp2d":
+        p = synth.exp2d_problem(2048)
+    elif name == "laplace":
+        p = synth.laplace_problem(3000)
+    else:
+        p = synth.matern_problem(2500, 101)
+    Hp = hg.build_kernel_hmatrix(p.points, p.kind, 1e-6, scale=p.params.get("scale", 1.0), diag=p.params["diag"])
+    Ho = ohm.build_hmatrix(p, 1e-6, method="aca")
+    assert np.array_equal(Hp.perm, Ho.perm)
+    st = Hp.structure()
+    so = np.array([(b.row0, b.nrows, b.col0, b.ncols, b.kind) for b in Ho.blocks])
+    assert np.array_equal(st[:, :5], so)
+    ro = np.array([b.rank for b in Ho.blocks])
+    # ACA pivots may differ by rounding; ranks after recompression agree up to one
+    assert np.max(np.abs(st[:, 5] - ro)) <= 1
+    worst = 0.0
+    for i in np.flatnonzero(st[:, 4] == 1):
+        b = Hp.block(i)
+        if b["S"].size == 0:
+            continue
+        M = p.entries(Hp.perm[b["row0"]:b["row0"] + b["nrows"]], Hp.perm[b["col0"]:b["col0"] + b["ncols"]])
+        worst = max(worst, np.linalg.norm(M - (b["W"] * b["S"]) @ b["X"].T, 2) / np.linalg.norm(M, 2))
+        assert np.allclose(b["W"].T @ b["W"], np.eye(b["S"].size), atol=1e-10)
+    assert worst <= 3e-6
+    for i in np.flatnonzero(st[:, 4] == 0)[:50]:
+        b = Hp.block(i)
+        M = p.entries(Hp.perm[b["row0"]:b["row0"] + b["nrows"]], Hp.perm[b["col0"]:b["col0"] + b["ncols"]])
+        np.testing.assert_allclose(b["D"], M, rtol=1e-13, atol=0)
+
+
+def _tiny_blocks():
+    g = np.random.default_rng(0)
+    D = lambda r, c: g.standard_normal((r, c))
+    return [
+        {"row0": 0, "nrows": 3, "col0": 0, "ncols": 3, "kind": 0, "D": D(3, 3)},
+        {"row0": 0, "nrows": 3, "col0": 3, "ncols": 2, "kind": 0, "D": D(3, 2)},
+        {"row0": 3, "nrows": 2, "col0": 0, "ncols": 5, "kind": 0, "D": D(2, 5)},
+    ]
+
+
+def test_upload_rejects_invalid_descriptors():
+    bl = _tiny_blocks()
+    bad_cover = [dict(b) for b in bl[:2]]
+    with pytest.raises(hg.HlrError, match="cover"):
+        hg.upload(5, None, bad_cover, 1e-6)
+    overlap = [dict(b) for b in bl] + [dict(bl[0])]
+    with pytest.raises(hg.HlrError, match="cover"):
+        hg.upload(5, None, overlap, 1e-6)
+    with pytest.raises(hg.HlrError, match="permutation"):
+        hg.upload(5, [0, 1, 2, 3, 3], bl, 1e-6)
+    nan = [dict(b) for b in bl]
+    nan[0]["D"] = nan[0]["D"].copy()
+    nan[0]["D"][1, 1] = np.nan
+    with pytest.raises(hg.HlrError, match="NaN"):
+        hg.upload(5, None, nan, 1e-6)
+    with pytest.raises(hg.HlrError, match="eps"):
+        hg.upload(5, None, bl, 0.0)
+    lr = [dict(b) for b in bl]
+    lr[2] = {"row0": 3, "nrows": 2, "col0": 0, "ncols": 5, "kind": 1, "W": np.ones((2, 1)),
+             "S": np.array([-1.0]), "X": np.ones((5, 1))}
+    with pytest.raises(hg.HlrError, match="sigma"):
+        hg.upload(5, None, lr, 1e-6)
+    oob = [dict(b) for b in bl]
+    oob[1] = dict(oob[1], ncols=3)
+    with pytest.raises(hg.HlrError, match="out of range"):
+        hg.upload(5, None, oob, 1e-6)
+
+
+def test_host_errors_have_messages():
+    with pytest.raises(hg.HlrError) as ei:
+        hg.afl_encode(np.array([1.0, np.inf]), 1e-3)
+    assert "non-finite" in str(ei.value)
+    with pytest.raises(hg.HlrError):
+        hg.build_kernel_hmatrix(np.zeros((4, 2)), "exp2d", 0.0, scale=1.0)
