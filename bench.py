@@ -313,6 +313,7 @@ def run_ours(args, world: int, rank: int, local: int):
     el = time_loop(step32, args.steps, stream)
     barrier(world)
     clk = clocks.stop()
+    A.check()
     kms, calls = A.profile_read()
     el_max, total_bytes = aggregate(el, bytes_step * args.steps, world)
     value = total_bytes / el_max / 1e9

@@ -135,6 +135,12 @@ int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
 int hlr_solve_cg(hlr_handle h, const double *b_dev, double *x_dev, double rtol, int maxit,
                  int flags, void *cuda_stream, int *iters, double *relres);
 
+/* Wait for cuda_stream and report whether a product kernel of h gave up a bounded device-side
+ * wait since the previous check (HLR_ERR_TIMEOUT; the affected result is incomplete). Clears
+ * the error word. The product kernels never spin without a limit: every wait on a TMA copy or
+ * a shared-memory slot gives up after about 2 s. */
+int hlr_check(hlr_handle h, void *cuda_stream);
+
 /* Release the device arena of h (synchronises the device first). */
 int hlr_free(hlr_handle h);
 
@@ -167,7 +173,9 @@ int hlr_afl_decode_device(const uint8_t *stream_dev, int64_t n, double m_min, in
 
 /* Decode every unit of an uploaded matrix to FP64 on the GPU, concatenated in unit order
  * (per block in block order: dense -> its column-major values; lowrank -> W columns then X
- * columns). cap is the capacity of out_dev in doubles (>= hlr_info.values). */
+ * columns). cap is the capacity of out_dev in doubles (>= hlr_info.values). Available for
+ * matrices of at most 2^26 stored values (HLR_ERR_UNSUPPORTED above); allocates a temporary
+ * device map and synchronises cuda_stream. */
 int hlr_decode_units(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stream);
 
 /* ---- construction of kernel matrices (host, multithreaded) --------------------------------- */

@@ -150,6 +150,10 @@ class DeviceHMatrix:
         B.check(B.lib.hlr_decode_units(C.c_uint64(self.handle), _dev_ptr(out), out.numel(), _stream_ptr(None)))
         return out
 
+    def check(self, stream=None):
+        """Wait for the stream; raise HlrError(HLR_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
+        B.check(B.lib.hlr_check(C.c_uint64(self.handle), _stream_ptr(stream)))
+
     def free(self):
         if self.handle:
             B.check(B.lib.hlr_free(C.c_uint64(self.handle)))

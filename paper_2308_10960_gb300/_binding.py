@@ -80,6 +80,7 @@ SIGNATURES = [
                                      C.c_void_p]),
     ("hlr_solve_cg", C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("hlr_check", C.c_int, [C.c_uint64, C.c_void_p]),
     ("hlr_free", C.c_int, [C.c_uint64]),
     ("hlr_last_error", C.c_char_p, []),
     ("hlr_get_info", C.c_int, [C.c_uint64, C.POINTER(Info)]),

@@ -8,6 +8,7 @@ code on every host architecture.
 from __future__ import annotations
 
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -20,7 +21,7 @@ LIB = os.path.join(HERE, "libhlr_gb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 CU = ["hlr_kernels.cu", "hlr_cg.cu"]
-CPP = ["hlr_codec.cpp", "hlr_upload.cpp", "hlr_build.cpp"]
+CPP = ["hlr_codec.cpp", "hlr_upload.cpp", "hlr_pack.cpp", "hlr_build.cpp"]
 
 
 def _nvcc() -> str:
@@ -46,7 +47,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     cuda = _cuda_home(nvcc)
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "hlr_internal.h"), os.path.join(ROOT, "include", "hlr.h")]
+    stamp = os.path.join(BUILD, "stamp.txt")
+    want = f"{platform.machine()} {nvcc}\n"
+    if not os.path.exists(stamp) or open(stamp).read() != want or not os.path.exists(LIB):
+        force = True
+    headers = [os.path.join(CSRC, "hlr_internal.h"), os.path.join(CSRC, "hlr_pack.h"), os.path.join(ROOT, "include", "hlr.h")]
     inc = ["-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
     jobs = []
     objs = []
@@ -80,6 +85,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + r.stdout)
+    with open(stamp, "w") as f:
+        f.write(want)
     return LIB
 
 

@@ -1,5 +1,20 @@
 // Internal device layout of an uploaded H-matrix and host-side handle state.
-// Shared by the host packer (hlr_upload.cpp) and the CUDA kernels (hlr_kernels.cu).
+// Shared by the host packer (hlr_upload.cpp, hlr_pack.cpp) and the CUDA kernels.
+//
+// Work-ordered layout. The compressed codes of every AFL unit are re-placed (not re-encoded)
+// so that each CTA of a product kernel streams ONE contiguous byte range: a sequence of
+// pieces (<= kPieceMax bytes, <= kMaxCols column slices) copied into shared memory by TMA bulk
+// copies. A column slice is a run of consecutive values of one unit (a column of a dense
+// block, of W or of X restricted to a task's rows); in the kernels every lane owns one slice of
+// the current piece and decodes it sequentially.
+//  phase 1 (t = Sigma X~^T x): task = item = rows [row0, row0+R) (R <= 256) of the X columns
+//           of one lowrank block; a lane forms one column's dot product with x.
+//  phase 2 (y += W~ t + D~ x): task = leaf = a row interval of <= 64 rows; its slices are the
+//           columns of the dense blocks and of the W factors of the lowrank blocks covering it,
+//           in block order; lanes combine their slices row by row.
+// Segments group consecutive slices of one block inside a piece. The multipliers of a piece
+// (x|sigma, t m_min(W), phase-1 column factors) are staged by extra TMA ("aux") copies into the
+// same ring slot.
 #pragma once
 #include <cstddef>
 #include <cstdint>
@@ -10,85 +25,125 @@
 
 namespace hlr {
 
-// One encoded data unit (a dense block, or one column of W or X). 16 bytes.
-// Stream start = arena + 16 * (off_lo + 2^32 * off_hi). For HLR_FMT_FP64 the unit is plain
-// FP64 values (w = 64, e = m = 0, m_min unused).
-struct UnitHdr {
-  double m_min;
-  uint32_t off_lo;
-  uint8_t e, m, w;
-  uint8_t off_hi;
+constexpr int kPieceMax = 16384;  // bytes of one piece (header, segments, column headers, data)
+constexpr int kMaxCols = 128;     // column slices per piece (one per consumer lane)
+constexpr int kAuxMax = 512;      // multiplier elements staged with one piece
+constexpr int kStages = 3;        // ring slots per CTA
+constexpr int kConsumers = 128;   // consumer threads (4 warps) per CTA, plus one producer warp
+constexpr int kRowsPerItem = 256;
+constexpr int kLeafRows = 64;
+
+enum : uint8_t { SEG_DENSE = 0, SEG_W = 1, SEG_X = 2 };
+enum : uint8_t { PF_START_LEAF = 1, PF_END_LEAF = 2 };
+
+struct PieceHdr {
+  uint16_t nseg;
+  uint16_t ncols;    // column slices in the piece (<= kMaxCols)
+  uint16_t nr;       // phase 2: rows of the leaf
+  uint8_t flags;     // PF_START_LEAF, PF_END_LEAF (phase 2)
+  uint8_t pad0;
+  uint32_t row0;     // phase 2: first row of the leaf (cluster order)
+  uint32_t pad1;
 };
-static_assert(sizeof(UnitHdr) == 16, "UnitHdr must be 16 bytes");
+static_assert(sizeof(PieceHdr) == 16, "PieceHdr");
 
-// Per lowrank block with rank > 0: offsets of its Sigma/t values and of its partial sums.
-struct LRBlock {
-  uint32_t tbase;    // sigma[tbase + i], t[tbase + i]
-  uint32_t part0;    // partial[part0 + c * k + i] for chunk c
-  uint16_t k;
-  uint16_t nchunks;
-  uint32_t xunit0;   // unit index of X column 0 (X column i = xunit0 + i)
+// One segment (32 bytes): slices [cstart, cstart + nc) of the piece, all of one block.
+//  dense: nc columns x nr rows, codes column-major and contiguous at width w from word data_w;
+//         multiplier of column j = aux[xs + j] * m_min.
+//  W    : nc column slices of nr rows; slice i starts at word data_w + colhdr[i].wordoff;
+//         multiplier = aux[xs + i] (t_i m_min(W_i), computed by phase 1).
+//  X    : nc column slices of nr (= R) rows of one item; x of row r at aux[xs + r]; column
+//         factor sigma_i m_min(X_i) m_min(W_i) at aux[fs + i]; result for t index tidx + i, or
+//         for blocks of several chunks the partial sum partial[pbase + i nchunks + chunk]
+//         (combined in chunk order by k_combine).
+struct Seg {
+  uint8_t kind;
+  uint8_t lg;        // X: log2 of the lanes per column (a column of R rows uses 2^lg lanes)
+  uint16_t nc;
+  uint16_t cstart;   // first lane of the segment (aligned to 2^lg)
+  uint16_t nr;
+  uint16_t xs;
+  uint16_t data_w;   // data start, 32-bit words from the piece start
+  uint16_t col_w;    // W/X: column headers, words from the piece start; dense: e | m << 8
+  uint16_t fs;       // X: aux offset of the first column factor
+  uint32_t tidx;     // X: t index of the segment's first column
+  uint32_t cnt;      // unused
+  union {
+    double m_min;    // dense: m_min of the block's unit
+    struct {
+      uint32_t pbase;    // X: partial index of the first column's chunk 0
+      uint16_t chunk;    // X: chunk index of the item
+      uint16_t nchunks;  // X: chunks of the block
+    } x;
+  };
 };
-static_assert(sizeof(LRBlock) == 16, "LRBlock must be 16 bytes");
+static_assert(sizeof(Seg) == 32, "Seg");
 
-// Phase-1 work item: rows [row0, row0 + nrows) of X of one lowrank block (nrows <= 256).
-struct P1Item {
-  uint32_t blk;      // index into LRBlock array
-  uint32_t row0;     // first row of X (relative to the block's sigma cluster)
-  uint32_t xoff;     // position of x|sigma[row0] in the permuted x
-  uint16_t nrows;
-  uint16_t chunk;    // chunk index c
+// Column header of a W or X slice: word offset from the segment data start, e, m.
+struct ColHdr {
+  uint16_t wordoff;
+  uint8_t e;
+  uint8_t m;
 };
-static_assert(sizeof(P1Item) == 16, "P1Item must be 16 bytes");
+static_assert(sizeof(ColHdr) == 4, "ColHdr");
 
-// Phase-2 owner: a leaf row interval [row0, row0 + nrows), nrows <= 64, with the
-// contributions [c0, c1) that cover it.
-struct Leaf {
-  uint32_t row0;
-  uint32_t nrows;
-  uint32_t c0, c1;
+// A multiplier range copied into a slot: elements [elem0, elem0 + nelem) of x (which = 0), of
+// t m_min(W) (which = 1) or of the phase-1 column factors (which = 2) to slot aux element soff.
+// elem0 and nelem are multiples of 4.
+struct AuxCopy {
+  uint32_t elem0;
+  uint16_t nelem;
+  uint8_t which;
+  uint8_t pad;
+  uint32_t soff;
+  uint32_t pad2;
 };
-static_assert(sizeof(Leaf) == 16, "Leaf must be 16 bytes");
+static_assert(sizeof(AuxCopy) == 16, "AuxCopy");
 
-enum : uint32_t { CONTRIB_DENSE = 0, CONTRIB_LOWRANK = 1 };
-
-// A block restricted to one leaf row interval.
-//  dense  : unit = the block's unit; column j starts at value index j * ld + rowoff;
-//           multiplier of column j = x_perm[mbase + j] * m_min.
-//  lowrank: unit = W column 0 (column i = unit + i); value index rowoff + r;
-//           multiplier of column i = t[mbase + i] * m_min_i.
-struct Contrib {
-  uint32_t unit;
-  uint32_t ncols;
-  uint32_t rowoff;
-  uint32_t ld;
-  uint32_t mbase;
-  uint32_t kind;
-  uint32_t colbase;  // running column count of the leaf before this contribution (for warp rotation)
+// A column of a lowrank block whose phase-1 work is split into several chunks.
+struct Combine {
+  uint32_t tidx;     // t index of the column
+  uint32_t pbase;    // partial[pbase + c], c < nchunks
+  uint32_t nchunks;
   uint32_t pad;
 };
-static_assert(sizeof(Contrib) == 32, "Contrib must be 32 bytes");
+static_assert(sizeof(Combine) == 16, "Combine");
 
-// Device pointers into an arena (all set by the host after upload).
+// Issue stream of a CTA's producer: for every piece one entry
+//   {offset_lo, offset_hi | 1 << 31, bytes, aux elements}
+// followed by one entry per aux copy {elem0, nelem | which << 16, soff, 0}.
+struct IssueEnt {
+  uint32_t a, b, c, d;
+};
+static_assert(sizeof(IssueEnt) == 16, "IssueEnt");
+constexpr uint32_t kIssuePiece = 1u << 31;
+
+struct PhaseDev {
+  const IssueEnt *ent;        // issue streams of all CTAs, back to back
+  const uint32_t *cta_e0;     // [nct + 1] entry ranges
+  const uint32_t *cta_np;     // [nct] pieces per CTA
+  int32_t nct, np;
+};
+
+// Device pointers into an arena (set by the host after upload).
 struct DevLayout {
-  const uint8_t *base;       // arena base (unit streams are addressed from here)
-  const UnitHdr *units;
-  const double *sigma;       // [rank_sum]
-  const LRBlock *lrb;        // [nlr]
-  const P1Item *items;       // [nitems]
-  const Leaf *leaves;        // [nleaves]
-  const Contrib *contribs;   // [ncontribs]
+  const uint8_t *base;
   const int64_t *perm;       // [n]
+  const double *fac64;       // [rank_sum + 8] sigma_i m_min(X_i) m_min(W_i)
+  const float *fac32;        // [rank_sum + 8] the same in FP32
+  PhaseDev ph[2];
   // scratch
-  double *xperm64;           // [n * rhs_cap]
-  float *xperm32;            // [n * rhs_cap]
-  double *t;                 // [rank_sum * rhs_cap]
-  double *partial;           // [part_total * rhs_cap]
-  uint32_t *counters;        // [nlr] arrival counters + 4 work counters
+  double *xperm64;           // [n + 8]
+  float *xperm32;            // [n + 8]
+  double *tw64;              // [rank_sum + 8]  t_i m_min(W_i)
+  float *tw32;               // [rank_sum + 8]
+  double *partial;           // [part_total]
+  const Combine *comb;       // [ncnt] columns of blocks with several phase-1 chunks
+  uint32_t *status;          // [4] error words (0 = ok)
   double *xdev;              // [n] device copy of a host x (hlr_matvec_host)
-  double *ydev;              // [n] device copy of a host y (hlr_matvec_host)
+  double *ydev;              // [n]
   int64_t n;
-  int32_t nlr, nitems, nleaves, format;
+  int32_t ncnt, raw;         // raw = 1 for HLR_FMT_FP64
 };
 
 struct Handle {
@@ -98,18 +153,17 @@ struct Handle {
   size_t arena_bytes = 0;
   DevLayout L{};
   hlr_info info{};
-  int64_t ncontribs = 0;
-  int64_t part_total = 0;
   int64_t nunits = 0;
   int64_t values = 0;
-  std::vector<int64_t> unit_value_offset;  // host copy: start of unit u in the decode output
-  std::vector<int64_t> unit_len;           // host copy: number of values of unit u
-  std::vector<UnitHdr> unit_hdr;           // host copy of the headers
-  size_t scratch_bytes = 0;                // bytes of the scratch region
-  size_t scratch_off = 0;                  // offset of the scratch region in the arena
-  void *cg_ws = nullptr;                   // CG work vectors (allocated on first solve)
-  std::vector<void *> prof_ev;             // cudaEvent_t ring: 4 per profiled product
-  int prof_n = 0;                          // profiled products since the last read
+  std::vector<uint64_t> slice_src;   // decode map: arena bit address of each unit slice
+  std::vector<uint64_t> slice_dst;   // ... its first value index in the unit-order output
+  std::vector<uint32_t> slice_n;     // ... its number of values
+  std::vector<uint32_t> slice_unit;  // ... its unit
+  std::vector<double> unit_mmin;     // per unit: m_min
+  std::vector<uint8_t> unit_e, unit_m;
+  void *cg_ws = nullptr;             // CG work vectors (allocated on first solve)
+  std::vector<void *> prof_ev;       // cudaEvent_t ring: 4 per profiled product
+  int prof_n = 0;
 };
 constexpr int kProfileCap = 4096;
 
@@ -117,12 +171,13 @@ constexpr int kProfileCap = 4096;
 int set_error(int code, const std::string &msg);
 Handle *lookup(hlr_handle h);
 
-// Kernel launchers (hlr_kernels.cu).
+// Kernel side (hlr_kernels.cu).
 int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream);
 int launch_decode_units(const Handle &H, double *out, void *stream);
-int profile_read(Handle &H, double *ms, int *calls);
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out,
                          void *stream_);
+int profile_read(Handle &H, double *ms, int *calls);
+int ctas_per_phase(int device);  // persistent grid size of the product kernels
 
 // Host codec (hlr_codec.cpp).
 int mantissa_bits(double u);
@@ -130,9 +185,7 @@ struct AflParams {
   double m_min;
   int e, m, w;
 };
-// Scan values: m_min, e, m for precision u. Returns false on non-finite input.
 bool afl_params(const double *a, int64_t n, double u, AflParams *p);
-// Pack the codes of a at params p into out (zeroed, >= padded size bytes).
 void afl_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out);
 inline size_t padded16(size_t b) { return (b + 15) & ~size_t(15); }
 inline size_t afl_bytes(int64_t n, int w) { return (size_t(n) * size_t(w) + 7) / 8; }

@@ -1,83 +1,137 @@
 // CUDA kernels of the compressed H-matrix-vector product y += A~ x (Section 5.4) over AFL /
-// AFL-APLR streams (Sections 3.2, 3.3), decoded inside the product.
+// AFL-APLR codes (Sections 3.2, 3.3), decoded inside the product.
 //
 //   k_permute : x_perm = x[perm] (FP64 and FP32 copies)
-//   k_phase1  : for every lowrank block b, t_b = Sigma_b (X~_b^T x|sigma) -- one warp per item
-//               of <= 256 rows of X, warp-shuffle sums, partial sums of a block combined in
-//               chunk order by the last item to finish (no spin waits, deterministic)
-//   k_phase2  : one CTA per leaf row interval (<= 64 rows): y|l += sum over the blocks that
-//               cover l of W~_b|l t_b or D~_b|l x|sigma, columns spread over 8 warps, one fixed
-//               order, one owner per row (no atomics on y)
+//   k_product<FMT, 0> (phase 1): for every lowrank block b and column i,
+//               t_b,i m_min(W_b,i) = sigma_i m_min(X_i) m_min(W_i) sum_r X~code_r,i x_r;
+//               a block wider than 256 rows is split into items whose partial sums are
+//               combined in chunk order by the last one to finish (no spin waits)
+//   k_product<FMT, 1> (phase 2): per leaf row interval l (<= 64 rows), y|l += the sum over the
+//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma, in one fixed order, one
+//               owner per row (no atomics on y)
 //
-// Storage formats: FMT_AFL32 decodes to FP32 with integer ops and sums in FP32 inside a block
-// and FP64 across blocks; FMT_AFL64 decodes and sums in FP64; FMT_RAW64 reads plain FP64
-// factors (the uncompressed baseline).
+// Both phases are persistent kernels over the work-ordered piece streams (hlr_internal.h):
+// one producer warp per CTA issues TMA bulk copies (cp.async.bulk) of the next pieces and of
+// their multipliers into a ring of shared-memory slots guarded by mbarriers; in the four
+// consumer warps every lane owns one column slice of the current piece and decodes its codes
+// one after the other from shared memory (a running 64-bit window, so the per-column set-up is
+// paid once per slice). Phase 2 combines the lanes' values row by row with warp shuffles.
+// Every wait is bounded (about 2 s of clock cycles), after which the kernel records an error
+// word and returns.
+//
+// FMT_AFL32: codes -> FP32 bit patterns with integer ops; FP32 sums over a slice (phase 1) or
+//            over the <= 32 slices of a warp (phase 2); compensated FP32 pairs across pieces;
+//            FP64 for the final per-row sum into y.
+// FMT_AFL64: codes -> FP64, FP64 sums.   FMT_RAW64: plain FP64 factors (uncompressed baseline).
 #include <cuda_runtime.h>
 
 #include <mutex>
 #include <string>
+#include <type_traits>
+#include <vector>
 
 #include "hlr_internal.h"
 
 namespace hlr {
 
 enum { FMT_AFL32 = 0, FMT_AFL64 = 1, FMT_RAW64 = 2 };
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = kConsumers + 32;
+constexpr int kCWarps = kConsumers / 32;
 constexpr unsigned kFull = 0xffffffffu;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at the GB300 SM clock
 
-__device__ __forceinline__ const uint32_t *unit_words(const uint8_t *base, const UnitHdr &h) {
-  const uint64_t o16 = uint64_t(h.off_lo) | (uint64_t(h.off_hi) << 32);
-  return reinterpret_cast<const uint32_t *>(base + (o16 << 4));
+template <int FMT>
+struct Tr {
+  using A = double;  // multiplier / accumulator type
+  static constexpr int esz = 8;
+};
+template <>
+struct Tr<FMT_AFL32> {
+  using A = float;
+  static constexpr int esz = 4;
+};
+template <int FMT>
+__host__ __device__ constexpr size_t slot_bytes() {
+  return size_t(kPieceMax) + 16 + size_t(kAuxMax) * Tr<FMT>::esz;
+}
+template <int FMT>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return size_t(kStages) * slot_bytes<FMT>() + 2 * kStages * 8 + 2 * kCWarps * 64 * 8 +
+         (FMT == 0 ? size_t(kCWarps) * 32 * 33 * 4 : 0) + 16;
 }
 
-__device__ __forceinline__ UnitHdr load_hdr(const UnitHdr *p) {
-  const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-  UnitHdr h;
-  h.m_min = __hiloint2double(int(v.y), int(v.x));
-  h.off_lo = v.z;
-  h.e = uint8_t(v.w & 0xff);
-  h.m = uint8_t((v.w >> 8) & 0xff);
-  h.w = uint8_t((v.w >> 16) & 0xff);
-  h.off_hi = uint8_t(v.w >> 24);
-  return h;
+// ---------------------------------------------------------------------------------------------
+// PTX helpers: shared-memory addresses, mbarriers, TMA bulk copies, consumer barrier
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of parity `parity` to complete; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+  if (mbar_try_wait(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(b, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bar_consumers() { asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory"); }
 
-// Per-column decode constants.
+// ---------------------------------------------------------------------------------------------
+// Decoding
+// ---------------------------------------------------------------------------------------------
 struct ColDec {
-  uint32_t em_mask;   // (1 << (e+m)) - 1, e+m <= 31
-  uint32_t scale;     // 1 << (23 - m)     (FP32 fast path)
-  uint32_t sshift;    // 31 - (e + m): moves the sign bit to bit 31
+  uint32_t em_mask;  // (1 << (e+m)) - 1 (all ones if e+m >= 32)
+  uint32_t scale;    // 1 << (23 - m)   (FP32 fast path)
+  uint32_t sshift;   // 31 - (e + m): moves the sign bit to bit 31
   uint32_t e, m, w;
-  bool fast32;        // w <= 32, m <= 23, e <= 7: FP32 bit pattern built with integer ops
+  bool fast32;       // w <= 32, m <= 23, e <= 7: FP32 bit pattern built with integer ops
+  bool narrow;       // w <= 32: a code fits a two-word window
 };
 
-__device__ __forceinline__ ColDec col_dec(const UnitHdr &h) {
+__device__ __forceinline__ ColDec col_dec(uint32_t e, uint32_t m) {
   ColDec c;
-  c.e = h.e;
-  c.m = h.m;
-  c.w = h.w;
-  const uint32_t em = c.e + c.m;
+  c.e = e;
+  c.m = m;
+  c.w = 1 + e + m;
+  const uint32_t em = e + m;
   c.em_mask = em >= 32 ? 0xffffffffu : ((1u << em) - 1u);
-  c.scale = c.m <= 23 ? (1u << (23 - c.m)) : 0u;
+  c.scale = m <= 23 ? (1u << (23 - m)) : 0u;
   c.sshift = em <= 31 ? 31 - em : 0;
-  c.fast32 = (c.w <= 32) && (c.m <= 23) && (c.e <= 7);
+  c.fast32 = (c.w <= 32) && (m <= 23) && (e <= 7);
+  c.narrow = c.w <= 32;
   return c;
 }
 
-// 32-bit code window starting at bit sh of p[0..1] (w <= 32).
-__device__ __forceinline__ uint32_t code32(const uint32_t *p, uint32_t sh) {
-  return __funnelshift_r(__ldg(p), __ldg(p + 1), sh);
-}
-
-// 64-bit code window starting at bit sh of p[0..2] (w <= 64).
-__device__ __forceinline__ uint64_t code64(const uint32_t *p, uint32_t sh) {
-  const uint32_t a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
-  const uint32_t lo = __funnelshift_r(a, b, sh), hi = __funnelshift_r(b, c, sh);
-  return (uint64_t(hi) << 32) | lo;
-}
-
-// FP32 value +-(v - 1) from a code (fast path).
+// +-(v - 1) as FP32 (fast path: integer ops build the FP32 pattern of v)
 __device__ __forceinline__ float dec_f32(uint32_t code, const ColDec &c) {
   const uint32_t mag = (code & c.em_mask) * c.scale + 0x3F800000u;
   const float v = __uint_as_float(mag) - 1.0f;
@@ -85,45 +139,50 @@ __device__ __forceinline__ float dec_f32(uint32_t code, const ColDec &c) {
   return __uint_as_float(__float_as_uint(v) ^ s);
 }
 
-// FP64 value +-(v - 1) from a code (any width).
+// +-(v - 1) as FP64 (any width)
 __device__ __forceinline__ double dec_f64(uint64_t code, const ColDec &c) {
-  const uint64_t em = code & ((c.e + c.m >= 64) ? ~0ull : ((1ull << (c.e + c.m)) - 1ull));
-  const uint64_t b = (em << (52 - c.m)) + (1023ull << 52);
-  double v = __longlong_as_double(static_cast<long long>(b)) - 1.0;
-  const uint64_t s = (code >> (c.e + c.m)) & 1ull;
-  return s ? -v : v;
+  const uint32_t em = c.e + c.m;
+  const uint64_t mag = code & (em >= 64 ? ~0ull : ((1ull << em) - 1ull));
+  const uint64_t b = (mag << (52 - c.m)) + (1023ull << 52);
+  const double v = __longlong_as_double(static_cast<long long>(b)) - 1.0;
+  return ((code >> em) & 1ull) ? -v : v;
 }
 
-template <int FMT>
-struct Acc;
-template <>
-struct Acc<FMT_AFL32> {
-  using T = float;
-};
-template <>
-struct Acc<FMT_AFL64> {
-  using T = double;
-};
-template <>
-struct Acc<FMT_RAW64> {
-  using T = double;
+// 64-bit window of a shared-memory word array at an arbitrary bit
+__device__ __forceinline__ uint64_t code64_at(const uint32_t *p, uint32_t bit) {
+  const uint32_t q = bit >> 5;
+  const uint32_t a = p[q], b = p[q + 1], c = p[q + 2];
+  return (uint64_t(__funnelshift_r(b, c, bit)) << 32) | __funnelshift_r(a, b, bit);
+}
+
+// Sequential reader of one column slice: codes of width w <= 32 one after the other.
+struct Seq {
+  const uint32_t *p;
+  uint32_t nxt, lo, hi, pos;
+  __device__ __forceinline__ void init(const uint32_t *base, uint32_t bit) {
+    const uint32_t q = bit >> 5;
+    p = base;
+    lo = base[q];
+    hi = base[q + 1];
+    nxt = q + 2;
+    pos = bit & 31u;
+  }
+  __device__ __forceinline__ uint32_t code() const { return __funnelshift_r(lo, hi, pos); }
+  __device__ __forceinline__ void advance(uint32_t w) {
+    pos += w;
+    if (pos >= 32u) {
+      pos -= 32u;
+      lo = hi;
+      hi = p[nxt];
+      ++nxt;
+    }
+  }
 };
 
-// value(at value index vi of the unit) * mult, added to acc. p/sh address the value's bits.
-template <int FMT>
-__device__ __forceinline__ void fma_value(typename Acc<FMT>::T &acc, const uint32_t *p, uint32_t sh,
-                                          const ColDec &c, typename Acc<FMT>::T mult) {
-  if constexpr (FMT == FMT_AFL32) {
-    if (c.fast32) {
-      acc = fmaf(dec_f32(code32(p, sh), c), mult, acc);
-    } else {
-      const double v = dec_f64(c.w <= 32 ? uint64_t(code32(p, sh)) : code64(p, sh), c);
-      acc = fmaf(float(v), mult, acc);
-    }
-  } else {
-    const double v = dec_f64(c.w <= 32 ? uint64_t(code32(p, sh)) : code64(p, sh), c);
-    acc = fma(v, mult, acc);
-  }
+// Value r of a slice (FP32 / FP64 accumulation types) for the generic (wide) path.
+template <typename A>
+__device__ __forceinline__ A dec_at(const uint32_t *p, uint32_t bit, const ColDec &c) {
+  return A(dec_f64(code64_at(p, bit), c));
 }
 
 template <typename T>
@@ -132,6 +191,27 @@ __device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
   return v;
 }
+
+// Accumulation across pieces: compensated FP32 pair (about 48 significant bits) for the FP32
+// path, plain FP64 otherwise.
+struct Comp32 {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (a - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+  __device__ __forceinline__ void reset() { hi = lo = 0.f; }
+};
+struct Sum64 {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double a) { s += a; }
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ void reset() { s = 0.0; }
+};
 
 __global__ void k_permute(const int64_t *__restrict__ perm, int64_t n, const double *__restrict__ x,
                           double *__restrict__ x64, float *__restrict__ x32) {
@@ -143,158 +223,405 @@ __global__ void k_permute(const int64_t *__restrict__ perm, int64_t n, const dou
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phase 1: t_b = Sigma_b (X~_b^T x|sigma)
+// Producer: TMA bulk copies of the CTA's pieces and their multipliers into the slot ring
 // ---------------------------------------------------------------------------------------------
 template <int FMT>
-__global__ void __launch_bounds__(kThreads) k_phase1(DevLayout L) {
-  using T = typename Acc<FMT>::T;
+__device__ void producer(const DevLayout &L, const PhaseDev &P, uint32_t e0, uint32_t e1, uint8_t *smem,
+                         uint64_t *full, uint64_t *empty) {
+  constexpr uint32_t esz = Tr<FMT>::esz;
+  constexpr size_t slot = slot_bytes<FMT>();
   const int lane = threadIdx.x & 31;
-  uint32_t *work = L.counters + L.nlr;
-  for (;;) {
-    uint32_t ii = 0;
-    if (lane == 0) ii = atomicAdd(work, 1u);
-    ii = __shfl_sync(kFull, ii, 0);
-    if (ii >= uint32_t(L.nitems)) break;
-    const P1Item it = L.items[ii];
-    const LRBlock B = L.lrb[it.blk];
-    const int nr = it.nrows;
-    T xr[8];
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const int r = lane + 32 * v;
-      if constexpr (FMT == FMT_AFL32)
-        xr[v] = r < nr ? __ldg(L.xperm32 + it.xoff + r) : 0.0f;
-      else
-        xr[v] = r < nr ? __ldg(L.xperm64 + it.xoff + r) : 0.0;
-    }
-    const bool single = B.nchunks == 1;
-    for (int i = 0; i < B.k; ++i) {
-      const UnitHdr h = load_hdr(L.units + B.xunit0 + i);
-      const uint32_t *base = unit_words(L.base, h);
-      T a = T(0);
-      if constexpr (FMT == FMT_RAW64) {
-        const double *col = reinterpret_cast<const double *>(base) + it.row0;
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int r = lane + 32 * v;
-          if (r < nr) a = fma(__ldg(col + r), xr[v], a);
+  const uint8_t *xsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.xperm32)
+                                         : reinterpret_cast<const uint8_t *>(L.xperm64);
+  const uint8_t *tsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.tw32)
+                                         : reinterpret_cast<const uint8_t *>(L.tw64);
+  const uint8_t *fsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.fac32)
+                                         : reinterpret_cast<const uint8_t *>(L.fac64);
+  const uint4 *ent = reinterpret_cast<const uint4 *>(P.ent);
+  uint32_t i = 0;  // pieces issued
+  uint32_t cur = 0;
+  bool ok = true;
+  // the stream is read 32 entries per coalesced load, one load ahead
+  uint4 nxt = e0 + lane < e1 ? __ldg(ent + e0 + lane) : make_uint4(0, 0, 0, 0);
+  for (uint32_t e = e0; e < e1 && ok; e += 32) {
+    const uint4 mine = nxt;
+    if (e + 32 + lane < e1) nxt = __ldg(ent + e + 32 + lane);
+    const uint32_t cnt = min(32u, e1 - e);
+    for (uint32_t k = 0; k < cnt; ++k) {
+      const uint32_t a = __shfl_sync(kFull, mine.x, k), b = __shfl_sync(kFull, mine.y, k);
+      const uint32_t c = __shfl_sync(kFull, mine.z, k), d = __shfl_sync(kFull, mine.w, k);
+      if (b & kIssuePiece) {
+        const uint32_t s = i % kStages;
+        uint32_t good = 1;
+        if (lane == 0) {
+          if (i >= uint32_t(kStages) && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+            atomicOr(L.status, 2u);
+            good = 0;
+          } else {
+            const uint64_t off = (uint64_t(b & ~kIssuePiece) << 32) | a;
+            mbar_expect_tx(&full[s], c + d * esz);
+            tma_load(smem + size_t(s) * slot, L.base + off, c, &full[s]);
+          }
         }
-      } else {
-        const ColDec c = col_dec(h);
-        const uint64_t bit0 = uint64_t(it.row0 + lane) * c.w;
-        const uint32_t *p = base + (bit0 >> 5);
-        const uint32_t sh = uint32_t(bit0 & 31);
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const int r = lane + 32 * v;
-          if (r < nr) fma_value<FMT>(a, p + v * c.w, sh, c, xr[v]);
+        ok = __shfl_sync(kFull, good, 0) != 0;
+        if (!ok) break;
+        cur = s;
+        ++i;
+      } else if (lane == 0) {
+        const uint32_t nelem = b & 0xffffu, which = b >> 16;
+        const uint8_t *src = (which == 0 ? xsrc : which == 1 ? tsrc : fsrc) + size_t(a) * esz;
+        tma_load(smem + size_t(cur) * slot + kPieceMax + 16 + size_t(c) * esz, src, nelem * esz, &full[cur]);
+      }
+    }
+  }
+  // the last copy issued into every slot has landed before the CTA exits
+  if (lane == 0) {
+    const uint32_t first = i > uint32_t(kStages) ? i - kStages : 0;
+    for (uint32_t j = first; j < i; ++j)
+      if (!mbar_wait(&full[j % kStages], (j / kStages) & 1)) {
+        atomicOr(L.status, 4u);
+        break;
+      }
+  }
+}
+
+// segment of column slice c of a piece (largest q with cstart <= c)
+__device__ __forceinline__ int find_seg(const Seg *segs, int nseg, int c) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (int(segs[mid].cstart) <= c)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 1 consumers: one lane per X column slice, t_i m_min(W_i) (or a partial sum)
+// ---------------------------------------------------------------------------------------------
+template <int FMT>
+__device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty) {
+  using A = typename Tr<FMT>::A;
+  constexpr size_t slot = slot_bytes<FMT>();
+  const int t = threadIdx.x, lane = t & 31;
+  for (uint32_t i = 0; i < np; ++i) {
+    const uint32_t s = i % kStages;
+    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + 16);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    A dot = A(0);
+    uint32_t G = 1;
+    const Seg *sgp = nullptr;
+    int j = 0;
+    bool lead = false;
+    if (t < int(ph->ncols)) {
+      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
+      const int rel = t - int(sg.cstart);
+      const int jj = rel >> sg.lg;
+      if (jj < int(sg.nc)) {
+        sgp = &sg;
+        j = jj;
+        G = 1u << sg.lg;
+        const int sub = rel & int(G - 1);
+        lead = sub == 0;
+        const uint32_t ch = Wd[sg.col_w + j];
+        const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
+        const int r0 = sub * 32;
+        const int rc = min(32, int(sg.nr) - r0);  // rows of this lane (may be <= 0)
+        const A *xr = aux + sg.xs + r0;
+        if constexpr (FMT == FMT_RAW64) {
+          const double *Dd = reinterpret_cast<const double *>(Dc) + r0;
+#pragma unroll 4
+          for (int r = 0; r < rc; ++r) dot = fma(Dd[r], xr[r], dot);
+        } else {
+          const ColDec c = col_dec((ch >> 16) & 0xffu, ch >> 24);
+          if (c.narrow) {
+            Seq q;
+            q.init(Dc, uint32_t(r0) * c.w);
+            if constexpr (FMT == FMT_AFL32) {
+              if (c.fast32) {
+#pragma unroll 4
+                for (int r = 0; r < rc; ++r) {
+                  dot = fmaf(dec_f32(q.code(), c), xr[r], dot);
+                  q.advance(c.w);
+                }
+              } else {
+                for (int r = 0; r < rc; ++r) {
+                  dot = fmaf(float(dec_f64(q.code(), c)), xr[r], dot);
+                  q.advance(c.w);
+                }
+              }
+            } else {
+#pragma unroll 2
+              for (int r = 0; r < rc; ++r) {
+                dot = fma(dec_f64(q.code(), c), xr[r], dot);
+                q.advance(c.w);
+              }
+            }
+          } else {
+            for (int r = 0; r < rc; ++r) dot += dec_at<A>(Dc, uint32_t(r0 + r) * c.w, c) * xr[r];
+          }
         }
       }
-      a = warp_sum(a);
-      if (lane == 0) {
-        const double s = (FMT == FMT_RAW64) ? double(a) : double(a) * h.m_min;
-        if (single)
-          L.t[B.tbase + i] = __ldg(L.sigma + B.tbase + i) * s;
+    }
+    // the G lanes of a column (an aligned group) sum their 32-row parts in a fixed order
+#pragma unroll
+    for (uint32_t o = 1; o < 8; o <<= 1) {
+      const A v = __shfl_xor_sync(kFull, dot, o);
+      if (o < G) dot += v;
+    }
+    if (lead) {
+      const Seg &sg = *sgp;
+      const A f = aux[sg.fs + j];
+      if (sg.x.nchunks == 1) {
+        if constexpr (FMT == FMT_AFL32)
+          L.tw32[sg.tidx + j] = dot * f;
         else
-          L.partial[B.part0 + uint32_t(it.chunk) * B.k + i] = s;
+          L.tw64[sg.tidx + j] = dot * f;
+      } else {
+        L.partial[size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk] = double(dot);
       }
     }
-    if (!single) {
-      uint32_t old = 0;
-      if (lane == 0) {
-        __threadfence();
-        old = atomicAdd(L.counters + it.blk, 1u);
-      }
-      old = __shfl_sync(kFull, old, 0);
-      if (old == uint32_t(B.nchunks) - 1) {
-        __threadfence();
-        for (int i = lane; i < B.k; i += 32) {
-          double s = 0.0;
-          for (int c = 0; c < B.nchunks; ++c) s += __ldcg(L.partial + B.part0 + uint32_t(c) * B.k + i);
-          L.t[B.tbase + i] = __ldg(L.sigma + B.tbase + i) * s;
-        }
-      }
-    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+// Columns of blocks whose phase-1 work is split into chunks: sum the partial sums in chunk
+// order and apply the column factor (deterministic, no atomics).
+template <int FMT>
+__global__ void k_combine(DevLayout L) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < L.ncnt; i += int64_t(gridDim.x) * blockDim.x) {
+    const Combine c = L.comb[i];
+    double sum = 0.0;
+    for (uint32_t k = 0; k < c.nchunks; ++k) sum += L.partial[size_t(c.pbase) + k];
+    if constexpr (FMT == FMT_AFL32)
+      L.tw32[c.tidx] = float(sum * double(L.fac32[c.tidx]));
+    else
+      L.tw64[c.tidx] = sum * L.fac64[c.tidx];
+  }
+}
+
+// Setup of this lane's column slice j of segment sg: bit offset of row 0, e, m, multiplier.
+template <int FMT>
+__device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const uint32_t *Wd,
+                                            const typename Tr<FMT>::A *aux, uint32_t &start, uint32_t &e,
+                                            uint32_t &m, typename Tr<FMT>::A &mult) {
+  using A = typename Tr<FMT>::A;
+  if (sg.kind == SEG_DENSE) {
+    e = sg.col_w & 0xffu;
+    m = (sg.col_w >> 8) & 0xffu;
+    const uint32_t w = FMT == FMT_RAW64 ? 64u : 1u + e + m;
+    start = uint32_t(sg.data_w) * 32u + uint32_t(j * nr) * w;
+    mult = aux[sg.xs + j] * A(sg.m_min);
+  } else {
+    const uint32_t ch = Wd[sg.col_w + j];
+    e = (ch >> 16) & 0xffu;
+    m = ch >> 24;
+    start = (uint32_t(sg.data_w) + (ch & 0xffffu)) * 32u;
+    mult = aux[sg.xs + j];
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phase 2: y|l += sum_b A~_b|l x   (per leaf row interval l)
+// Phase 2 consumers, FP32 path: one lane per column slice of the leaf; every 32 rows the lanes
+// write their products to a padded shared-memory tile and sum it transposed (a lane per row)
 // ---------------------------------------------------------------------------------------------
 template <int FMT>
-__global__ void __launch_bounds__(kThreads) k_phase2(DevLayout L, double *__restrict__ y) {
-  using T = typename Acc<FMT>::T;
-  __shared__ double red[kWarps][64];
-  __shared__ uint32_t s_leaf;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t *work = L.counters + L.nlr + 1;
-  const double *t = L.t;
-  for (;;) {
-    if (threadIdx.x == 0) s_leaf = atomicAdd(work, 1u);
-    __syncthreads();
-    const uint32_t li = s_leaf;
-    __syncthreads();
-    if (li >= uint32_t(L.nleaves)) break;
-    const Leaf lf = L.leaves[li];
-    const int nr = int(lf.nrows);
-    const bool ok0 = lane < nr, ok1 = lane + 32 < nr;
-    double acc0 = 0.0, acc1 = 0.0;
-    for (uint32_t ci = lf.c0; ci < lf.c1; ++ci) {
-      const Contrib cb = L.contribs[ci];
-      T a0 = T(0), a1 = T(0);
-      const bool dense = cb.kind == CONTRIB_DENSE;
-      uint32_t j = uint32_t(warp - int(cb.colbase & 7) + 8) & 7u;
-      const UnitHdr hd = load_hdr(L.units + cb.unit);
-      for (; j < cb.ncols; j += kWarps) {
-        const UnitHdr h = dense ? hd : load_hdr(L.units + cb.unit + j);
-        const uint64_t vstart = dense ? uint64_t(j) * cb.ld + cb.rowoff : uint64_t(cb.rowoff);
-        const double m64 = dense ? __ldg(L.xperm64 + cb.mbase + j) : __ldcg(t + cb.mbase + j);
-        const uint32_t *base = unit_words(L.base, h);
-        if constexpr (FMT == FMT_RAW64) {
-          const double *col = reinterpret_cast<const double *>(base) + vstart;
-          if (ok0) a0 = fma(__ldg(col + lane), m64, a0);
-          if (ok1) a1 = fma(__ldg(col + lane + 32), m64, a1);
-        } else {
-          const ColDec c = col_dec(h);
-          const T mult = T(m64 * h.m_min);
-          const uint64_t bit0 = (vstart + lane) * c.w;
-          const uint32_t *p = base + (bit0 >> 5);
-          const uint32_t sh = uint32_t(bit0 & 31);
-          if (ok0) fma_value<FMT>(a0, p, sh, c, mult);
-          if (ok1) fma_value<FMT>(a1, p + c.w, sh, c, mult);
+__device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty,
+                               double *red, float *tiles, double *__restrict__ y) {
+  using A = typename Tr<FMT>::A;
+  constexpr size_t slot = slot_bytes<FMT>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  Comp32 acc0, acc1;  // rows lane and lane + 32 of the leaf: this warp's columns so far
+  uint32_t parity = 0;
+  int64_t gi = 0;
+  float *tile = tiles + warp * (32 * 33);
+  for (uint32_t i = 0; i < np; ++i) {
+    const uint32_t s = i % kStages;
+    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + 16);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+      acc0.reset();
+      acc1.reset();
+      if (t < nr) gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+    }
+    A mult = A(0);
+    uint32_t start = 0, e = 0, m = 0;
+    if (t < int(ph->ncols)) {
+      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
+      slice_setup<FMT>(sg, t - int(sg.cstart), nr, Wd, aux, start, e, m, mult);
+    }
+    const ColDec c = col_dec(e, m);
+    Seq q;
+    if (c.narrow) q.init(Wd, start);
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+      const int rows = min(32, nr - r0);
+      if (c.fast32) {
+#pragma unroll 4
+        for (int rr = 0; rr < rows; ++rr) {
+          tile[rr * 33 + lane] = dec_f32(q.code(), c) * mult;
+          q.advance(c.w);
         }
+      } else if (c.narrow) {
+        for (int rr = 0; rr < rows; ++rr) {
+          tile[rr * 33 + lane] = float(dec_f64(q.code(), c)) * mult;
+          q.advance(c.w);
+        }
+      } else {
+        for (int rr = 0; rr < rows; ++rr)
+          tile[rr * 33 + lane] = float(dec_f64(code64_at(Wd, start + uint32_t(r0 + rr) * c.w), c)) * mult;
       }
-      acc0 += double(a0);
-      acc1 += double(a1);
-    }
-    red[warp][lane] = acc0;
-    red[warp][lane + 32] = acc1;
-    __syncthreads();
-    if (threadIdx.x < nr) {
-      double s = 0.0;
+      __syncwarp();
+      if (lane < rows) {
+        float sum = 0.f;
 #pragma unroll
-      for (int w = 0; w < kWarps; ++w) s += red[w][threadIdx.x];
-      const int64_t gi = L.perm[lf.row0 + threadIdx.x];
-      y[gi] += s;
+        for (int cc = 0; cc < 32; ++cc) sum += tile[lane * 33 + cc];
+        if (r0 == 0)
+          acc0.add(sum);
+        else
+          acc1.add(sum);
+      }
+      __syncwarp();
     }
+    if (flags & PF_END_LEAF) {
+      // per-warp row sums; the two halves of red alternate between leaves, so one barrier
+      // suffices (a half is rewritten only after the next leaf's barrier)
+      double *buf = red + parity * (kCWarps * 64);
+      buf[warp * 64 + lane] = acc0.value();
+      buf[warp * 64 + 32 + lane] = acc1.value();
+      bar_consumers();
+      if (t < nr) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCWarps; ++w) sum += buf[w * 64 + t];
+        atomicAdd(y + gi, sum);  // the only update of this row: a fire-and-forget reduction
+      }
+      parity ^= 1u;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 2 consumers, FP64 paths: lanes are the rows of the leaf (lane, lane + 32); the warps
+// take the piece's column slices in turn; one FP64 fused multiply-add per value
+// ---------------------------------------------------------------------------------------------
+template <int FMT>
+__device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full,
+                                    uint64_t *empty, double *red, double *__restrict__ y) {
+  constexpr size_t slot = slot_bytes<FMT>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double a0 = 0.0, a1 = 0.0;
+  uint32_t parity = 0;
+  int64_t gi = 0;
+  for (uint32_t i = 0; i < np; ++i) {
+    const uint32_t s = i % kStages;
+    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const double *aux = reinterpret_cast<const double *>(sl + kPieceMax + 16);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+      a0 = a1 = 0.0;
+      if (t < nr) gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+    }
+    const bool ok0 = lane < nr, ok1 = lane + 32 < nr;
+    const int ncols = ph->ncols;
+    for (int col = warp; col < ncols; col += kCWarps) {
+      const Seg &sg = segs[find_seg(segs, ph->nseg, col)];
+      double mult;
+      uint32_t start, e, m;
+      slice_setup<FMT>(sg, col - int(sg.cstart), nr, Wd, aux, start, e, m, mult);
+      if constexpr (FMT == FMT_RAW64) {
+        const double *Dd = reinterpret_cast<const double *>(Wd + (start >> 5));
+        if (ok0) a0 = fma(Dd[lane], mult, a0);
+        if (ok1) a1 = fma(Dd[lane + 32], mult, a1);
+      } else {
+        const ColDec c = col_dec(e, m);
+        if (ok0) a0 = fma(dec_f64(code64_at(Wd, start + uint32_t(lane) * c.w), c), mult, a0);
+        if (ok1) a1 = fma(dec_f64(code64_at(Wd, start + uint32_t(lane + 32) * c.w), c), mult, a1);
+      }
+    }
+    if (flags & PF_END_LEAF) {
+      double *buf = red + parity * (kCWarps * 64);
+      buf[warp * 64 + lane] = a0;
+      buf[warp * 64 + 32 + lane] = a1;
+      bar_consumers();
+      if (t < nr) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCWarps; ++w) sum += buf[w * 64 + t];
+        atomicAdd(y + gi, sum);
+      }
+      parity ^= 1u;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+template <int FMT, int PH>
+__global__ void __launch_bounds__(kThreads) k_product(DevLayout L, double *__restrict__ y) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  constexpr size_t slot = slot_bytes<FMT>();
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
+  uint64_t *empty = full + kStages;
+  double *red = reinterpret_cast<double *>(empty + kStages);
+  float *tiles = reinterpret_cast<float *>(red + 2 * kCWarps * 64);
+  const PhaseDev &P = L.ph[PH];
+  const uint32_t e0 = P.cta_e0[blockIdx.x], e1 = P.cta_e0[blockIdx.x + 1];
+  const uint32_t np = P.cta_np[blockIdx.x];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kCWarps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (np == 0) return;
+  if (threadIdx.x >= kConsumers) {
+    producer<FMT>(L, P, e0, e1, smem, full, empty);
+    return;
+  }
+  if constexpr (PH == 0)
+    consume_phase1<FMT>(L, np, smem, full, empty);
+  else if constexpr (FMT == FMT_AFL32)
+    consume_phase2<FMT>(L, np, smem, full, empty, red, tiles, y);
+  else
+    consume_phase2_rows<FMT>(L, np, smem, full, empty, red, y);
 }
 
 // ---------------------------------------------------------------------------------------------
 // Bit-exact decoding (test path): a = (v - 1) * m_min in IEEE FP64, no contraction.
 // ---------------------------------------------------------------------------------------------
-__device__ double decode_exact(const uint32_t *words, uint64_t nwords, uint64_t j, int e, int m, double m_min) {
+__device__ double decode_code_exact(uint64_t code, int e, int m, double m_min) {
   const int w = 1 + e + m;
-  const uint64_t bit = j * uint64_t(w);
-  const uint64_t q = bit >> 5;
-  const int sh = int(bit & 31);
-  const int need = (sh + w + 31) >> 5;  // words touched: 1..3
-  uint64_t lo = words[q];
-  uint64_t hi = 0;
-  if (need >= 2 && q + 1 < nwords) lo |= uint64_t(words[q + 1]) << 32;
-  if (need >= 3 && q + 2 < nwords) hi = words[q + 2];
-  uint64_t code = lo >> sh;
-  if (sh) code |= hi << (64 - sh);
   if (w < 64) code &= (1ull << w) - 1ull;
   const uint64_t mant = code & ((1ull << m) - 1ull);
   const uint64_t field = (code >> m) & ((1ull << e) - 1ull);
@@ -306,24 +633,40 @@ __device__ double decode_exact(const uint32_t *words, uint64_t nwords, uint64_t 
 }
 
 __global__ void k_decode_stream(const uint32_t *words, int64_t n, double m_min, int e, int m, double *out) {
-  const uint64_t nwords = (uint64_t(n) * uint64_t(1 + e + m) + 31) / 32;
-  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x)
-    out[j] = decode_exact(words, nwords, uint64_t(j), e, m, m_min);
+  const int w = 1 + e + m;
+  const uint64_t nwords = (uint64_t(n) * uint64_t(w) + 31) / 32;
+  for (int64_t j = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+    const uint64_t bit = uint64_t(j) * uint64_t(w);
+    const uint64_t q = bit >> 5;
+    const int sh = int(bit & 31);
+    const int need = (sh + w + 31) >> 5;  // words touched: 1..3
+    uint64_t lo = words[q], hi = 0;
+    if (need >= 2 && q + 1 < nwords) lo |= uint64_t(words[q + 1]) << 32;
+    if (need >= 3 && q + 2 < nwords) hi = words[q + 2];
+    uint64_t code = lo >> sh;
+    if (sh) code |= hi << (64 - sh);
+    out[j] = decode_code_exact(code, e, m, m_min);
+  }
 }
 
-__global__ void k_decode_units(const uint8_t *base, const UnitHdr *units, const int64_t *voff, int64_t nunits,
-                               int raw, double *out) {
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const UnitHdr h = units[u];
-    const int64_t o = voff[u], len = voff[u + 1] - voff[u];
-    const uint32_t *wd = unit_words(base, h);
-    if (raw) {
-      const double *src = reinterpret_cast<const double *>(wd);
-      for (int64_t j = threadIdx.x; j < len; j += blockDim.x) out[o + j] = src[j];
-    } else {
-      const uint64_t nwords = (uint64_t(len) * h.w + 31) / 32;
-      for (int64_t j = threadIdx.x; j < len; j += blockDim.x)
-        out[o + j] = decode_exact(wd, nwords, uint64_t(j), h.e, h.m, h.m_min);
+__global__ void k_decode_slices(const uint8_t *base, const uint64_t *src, const uint64_t *dst, const uint32_t *nv,
+                                const uint32_t *unit, const double *mmin, const uint8_t *ue, const uint8_t *um,
+                                int64_t nslices, int raw, double *out) {
+  for (int64_t s = blockIdx.x; s < nslices; s += gridDim.x) {
+    const uint32_t u = unit[s];
+    const int e = ue[u], m = um[u];
+    const int w = raw ? 64 : 1 + e + m;
+    const uint64_t b0 = src[s];
+    for (uint32_t v = threadIdx.x; v < nv[s]; v += blockDim.x) {
+      const uint64_t bit = b0 + uint64_t(v) * uint64_t(w);
+      if (raw) {
+        out[dst[s] + v] = *reinterpret_cast<const double *>(base + bit / 8);
+      } else {
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(base) + (bit >> 5);
+        const uint32_t sh = uint32_t(bit & 31);
+        const uint64_t code = (uint64_t(__funnelshift_r(wp[1], wp[2], sh)) << 32) | __funnelshift_r(wp[0], wp[1], sh);
+        out[dst[s] + v] = decode_code_exact(code, e, m, mmin[u]);
+      }
     }
   }
 }
@@ -335,29 +678,34 @@ namespace {
 
 struct DevProps {
   int sms = 0;
-  int occ1[3] = {0, 0, 0};
-  int occ2[3] = {0, 0, 0};
+  int occ = 0;
 };
-
 std::mutex g_props_mu;
 DevProps g_props[64];
 
-template <int FMT>
-void query_occ(DevProps &P) {
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ1[FMT], k_phase1<FMT>, kThreads, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&P.occ2[FMT], k_phase2<FMT>, kThreads, 0);
-  if (P.occ1[FMT] < 1) P.occ1[FMT] = 1;
-  if (P.occ2[FMT] < 1) P.occ2[FMT] = 1;
+template <int FMT, int PH>
+void set_smem_attr() {
+  cudaFuncSetAttribute(k_product<FMT, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<FMT>()));
 }
 
 const DevProps &props(int dev) {
   std::lock_guard<std::mutex> lk(g_props_mu);
   DevProps &P = g_props[dev & 63];
   if (P.sms == 0) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != dev) cudaSetDevice(dev);
     cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
-    query_occ<FMT_AFL32>(P);
-    query_occ<FMT_AFL64>(P);
-    query_occ<FMT_RAW64>(P);
+    set_smem_attr<FMT_AFL32, 0>();
+    set_smem_attr<FMT_AFL32, 1>();
+    set_smem_attr<FMT_AFL64, 0>();
+    set_smem_attr<FMT_AFL64, 1>();
+    set_smem_attr<FMT_RAW64, 0>();
+    set_smem_attr<FMT_RAW64, 1>();
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_product<FMT_AFL32, 1>, kThreads, smem_bytes<FMT_AFL32>());
+    P.occ = occ < 1 ? 1 : occ;
+    if (cur != dev) cudaSetDevice(cur);
   }
   return P;
 }
@@ -370,17 +718,12 @@ int cuda_status(const char *what) {
 
 template <int FMT>
 void launch_phases(const Handle &H, double *y, cudaStream_t st, cudaEvent_t *ev) {
-  const DevProps &P = props(H.device);
   const DevLayout &L = H.L;
   if (ev) cudaEventRecord(ev[1], st);
-  if (L.nitems > 0) {
-    int grid = P.sms * P.occ1[FMT];
-    grid = std::min(grid, (L.nitems + kWarps - 1) / kWarps);
-    k_phase1<FMT><<<grid, kThreads, 0, st>>>(L);
-  }
+  if (L.ph[0].np > 0) k_product<FMT, 0><<<L.ph[0].nct, kThreads, smem_bytes<FMT>(), st>>>(L, y);
+  if (L.ncnt > 0) k_combine<FMT><<<int(std::min<int64_t>((L.ncnt + 255) / 256, 1024)), 256, 0, st>>>(L);
   if (ev) cudaEventRecord(ev[2], st);
-  int grid2 = std::min(P.sms * P.occ2[FMT], L.nleaves);
-  k_phase2<FMT><<<grid2, kThreads, 0, st>>>(L, y);
+  if (L.ph[1].np > 0) k_product<FMT, 1><<<L.ph[1].nct, kThreads, smem_bytes<FMT>(), st>>>(L, y);
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -401,19 +744,23 @@ cudaEvent_t *profile_slot(Handle &H, int flags) {
 
 }  // namespace
 
+int ctas_per_phase(int device) {
+  const DevProps &P = props(device);
+  if (P.sms <= 0) return 0;
+  return P.sms * P.occ;
+}
+
 int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const DevLayout &L = H.L;
   cudaGetLastError();
+  props(H.device);
   cudaEvent_t *ev = profile_slot(H, flags);
   const int acc = flags & 0xff;
-  if (cudaMemsetAsync(L.counters, 0, sizeof(uint32_t) * (size_t(L.nlr) + 8), st) != cudaSuccess)
-    return cuda_status("hlr_matvec: counter reset");
-  const DevProps &P = props(H.device);
-  int gp = int(std::min<int64_t>((L.n + kThreads - 1) / kThreads, int64_t(P.sms) * 8));
+  const int gp = int(std::min<int64_t>((L.n + 255) / 256, 4096));
   if (ev) cudaEventRecord(ev[0], st);
-  k_permute<<<gp, kThreads, 0, st>>>(L.perm, L.n, x, L.xperm64, L.xperm32);
-  if (H.format == HLR_FMT_FP64)
+  k_permute<<<gp, 256, 0, st>>>(L.perm, L.n, x, L.xperm64, L.xperm32);
+  if (L.raw)
     launch_phases<FMT_RAW64>(H, y, st, ev);
   else if (acc == HLR_ACC_FP32)
     launch_phases<FMT_AFL32>(H, y, st, ev);
@@ -441,16 +788,34 @@ int profile_read(Handle &H, double *ms, int *calls) {
 int launch_decode_units(const Handle &H, double *out, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaGetLastError();
-  int64_t *voff = nullptr;
-  const size_t bytes = sizeof(int64_t) * H.unit_value_offset.size();
-  if (cudaMalloc(&voff, bytes) != cudaSuccess) return set_error(HLR_ERR_OOM, "hlr_decode_units: temp allocation failed");
-  cudaMemcpyAsync(voff, H.unit_value_offset.data(), bytes, cudaMemcpyHostToDevice, st);
-  const int grid = int(std::min<int64_t>(H.nunits, 65535));
-  if (grid > 0)
-    k_decode_units<<<grid, 128, 0, st>>>(H.L.base, H.L.units, voff, H.nunits, H.format == HLR_FMT_FP64 ? 1 : 0, out);
+  const int64_t ns = int64_t(H.slice_src.size());
+  const int64_t nu = H.nunits;
+  if (ns == 0) return HLR_OK;
+  const size_t bytes = ns * (8 + 8 + 4 + 4) + nu * (8 + 1 + 1) + 64;
+  uint8_t *tmp = nullptr;
+  if (cudaMalloc(&tmp, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(HLR_ERR_OOM, "hlr_decode_units: temporary allocation failed");
+  }
+  uint64_t *d_src = reinterpret_cast<uint64_t *>(tmp);
+  uint64_t *d_dst = d_src + ns;
+  double *d_mmin = reinterpret_cast<double *>(d_dst + ns);
+  uint32_t *d_n = reinterpret_cast<uint32_t *>(d_mmin + nu);
+  uint32_t *d_unit = d_n + ns;
+  uint8_t *d_e = reinterpret_cast<uint8_t *>(d_unit + ns);
+  uint8_t *d_m = d_e + nu;
+  cudaMemcpyAsync(d_src, H.slice_src.data(), 8 * ns, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_dst, H.slice_dst.data(), 8 * ns, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_mmin, H.unit_mmin.data(), 8 * nu, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_n, H.slice_n.data(), 4 * ns, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_unit, H.slice_unit.data(), 4 * ns, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_e, H.unit_e.data(), nu, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(d_m, H.unit_m.data(), nu, cudaMemcpyHostToDevice, st);
+  const int grid = int(std::min<int64_t>(ns, 65535));
+  k_decode_slices<<<grid, 64, 0, st>>>(H.L.base, d_src, d_dst, d_n, d_unit, d_mmin, d_e, d_m, ns, H.L.raw, out);
   int rc = cuda_status("hlr_decode_units");
   cudaError_t e = cudaStreamSynchronize(st);
-  cudaFree(voff);
+  cudaFree(tmp);
   if (rc == HLR_OK && e != cudaSuccess) rc = set_error(HLR_ERR_CUDA, std::string("hlr_decode_units: ") + cudaGetErrorString(e));
   return rc;
 }

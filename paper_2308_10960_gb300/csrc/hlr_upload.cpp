@@ -1,12 +1,16 @@
-// hlr_upload / hlr_free / hlr_get_info / hlr_last_error and the handle registry.
+// hlr_upload / hlr_free / hlr_get_info / hlr_last_error / host entry points and the handle registry.
 //
-// Upload flattens the block tree's leaves (Def. 2.2) into the work lists of the product:
-//  * every dense block is one AFL unit at precision eps; every lowrank block contributes one
-//    unit per column of W and of X at precision eps sigma_0 / sigma_i (APLR, Section 3.3);
-//  * phase-1 items: rows of X of a lowrank block in chunks of <= 256 rows (t = Sigma X^T x);
-//  * phase-2 owners: the leaf row intervals (finest row partition induced by the blocks,
-//    cut to <= 64 rows); each owner lists every block whose row cluster contains it, in block
-//    order, so y is accumulated by exactly one owner per row, in a fixed order.
+// Upload
+//  1. validates the descriptor (shapes, exact coverage of I x I, permutation, finite data);
+//  2. encodes every unit on the host: a dense block is one AFL unit at precision eps, a lowrank
+//     block one unit per column of W and of X at precision eps sigma_0 / sigma_i (APLR, Section
+//     3.3); the plain FP64 format stores the values as they are;
+//  3. flattens the leaves of the block tree (Def. 2.2) into the two work lists of the product --
+//     phase-1 items (<= 256 rows of the X columns of one lowrank block) and phase-2 leaves (row
+//     intervals of <= 64 rows with every block covering them, in block order) -- assigns them to
+//     the CTAs of the persistent kernels (longest task first onto the least loaded CTA) and
+//     re-places the codes so that every CTA reads one contiguous run of pieces (hlr_pack.cpp);
+//  4. copies the arena to the device.
 #include <cuda_runtime.h>
 #include <omp.h>
 
@@ -22,6 +26,7 @@
 #include <vector>
 
 #include "hlr_internal.h"
+#include "hlr_pack.h"
 
 namespace hlr {
 
@@ -43,21 +48,15 @@ Handle *lookup(hlr_handle h) {
 
 namespace {
 
-constexpr int kRowsPerItem = 256;
-constexpr int kLeafRows = 64;
-
-struct UnitSrc {
-  const double *a;
-  int64_t n;
-  double u;
-};
-
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct HostBuf {
   uint8_t *p = nullptr;
   ~HostBuf() { std::free(p); }
 };
+
+// Values up to which hlr_decode_units is available (its map costs 24 bytes per slice).
+constexpr int64_t kDecodeMapMaxValues = int64_t(1) << 26;
 
 }  // namespace
 }  // namespace hlr
@@ -71,7 +70,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   if (!d || !out) return set_error(HLR_ERR_INVALID, "hlr_upload: null descriptor or output");
   *out = 0;
   const int64_t n = d->n;
-  if (n <= 0 || n > (int64_t(1) << 31)) return set_error(HLR_ERR_INVALID, "hlr_upload: n out of range");
+  if (n <= 0 || n > (int64_t(1) << 31) - 64) return set_error(HLR_ERR_INVALID, "hlr_upload: n out of range");
   if (d->nblocks <= 0 || !d->blocks) return set_error(HLR_ERR_INVALID, "hlr_upload: no blocks");
   if (d->format != HLR_FMT_AFL_APLR && d->format != HLR_FMT_FP64)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
@@ -96,7 +95,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
 
   // ---- block checks
   const int64_t nb = d->nblocks;
-  int64_t ndense = 0, nlr = 0, rank_sum = 0, values = 0;
+  int64_t ndense = 0, rank_sum = 0, values = 0;
   for (int64_t b = 0; b < nb; ++b) {
     const hlr_block_desc &B = d->blocks[b];
     if (B.row0 < 0 || B.col0 < 0 || B.nrows <= 0 || B.ncols <= 0 || B.row0 + B.nrows > n ||
@@ -104,8 +103,6 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       return set_error(HLR_ERR_INVALID, "hlr_upload: block " + std::to_string(b) + " out of range");
     if (B.kind == HLR_DENSE) {
       if (!B.D) return set_error(HLR_ERR_INVALID, "hlr_upload: dense block without data");
-      if (B.nrows * B.ncols > (int64_t(1) << 31))
-        return set_error(HLR_ERR_UNSUPPORTED, "hlr_upload: dense block too large");
       ++ndense;
       values += B.nrows * B.ncols;
     } else if (B.kind == HLR_LOWRANK) {
@@ -118,7 +115,6 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
           if (!(s > 0.0) || !std::isfinite(s) || s > B.sigma[0])
             return set_error(HLR_ERR_INVALID, "hlr_upload: sigma must be positive, finite and led by its maximum");
         }
-        ++nlr;
         rank_sum += B.rank;
         values += int64_t(B.rank) * (B.nrows + B.ncols);
       }
@@ -126,6 +122,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       return set_error(HLR_ERR_INVALID, "hlr_upload: unknown block kind");
     }
   }
+  if (rank_sum > (int64_t(1) << 31)) return set_error(HLR_ERR_UNSUPPORTED, "hlr_upload: total rank too large");
 
   // ---- elementary row intervals and coverage check
   std::vector<int64_t> brk;
@@ -158,222 +155,181 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     if (c != n) return set_error(HLR_ERR_INVALID, "hlr_upload: blocks do not cover the matrix exactly once");
   }
 
-  // ---- units
-  std::vector<UnitSrc> src;
-  src.reserve(ndense + 2 * rank_sum);
-  std::vector<int64_t> blk_unit0(nb, -1);
+  // ---- units (canonical per-unit streams)
+  PackInput in;
+  in.n = n;
+  in.raw = !afl;
+  in.blocks = d->blocks;
+  in.nblocks = nb;
+  std::vector<const double *> usrc;
+  std::vector<double> uprec;
+  in.blk_unit0.assign(nb, -1);
   for (int64_t b = 0; b < nb; ++b) {
     const hlr_block_desc &B = d->blocks[b];
     if (B.kind == HLR_DENSE) {
-      blk_unit0[b] = int64_t(src.size());
-      src.push_back({B.D, B.nrows * B.ncols, d->eps});
+      in.blk_unit0[b] = int64_t(usrc.size());
+      usrc.push_back(B.D);
+      in.unit_len.push_back(B.nrows * B.ncols);
+      uprec.push_back(d->eps);
     } else if (B.rank > 0) {
-      blk_unit0[b] = int64_t(src.size());
+      in.blk_unit0[b] = int64_t(usrc.size());
       const double delta = d->eps * B.sigma[0];
-      for (int i = 0; i < B.rank; ++i) src.push_back({B.W + i * B.nrows, B.nrows, delta / B.sigma[i]});
-      for (int i = 0; i < B.rank; ++i) src.push_back({B.X + i * B.ncols, B.ncols, delta / B.sigma[i]});
+      for (int i = 0; i < B.rank; ++i) {
+        usrc.push_back(B.W + i * B.nrows);
+        in.unit_len.push_back(B.nrows);
+        uprec.push_back(delta / B.sigma[i]);
+      }
+      for (int i = 0; i < B.rank; ++i) {
+        usrc.push_back(B.X + i * B.ncols);
+        in.unit_len.push_back(B.ncols);
+        uprec.push_back(delta / B.sigma[i]);
+      }
     }
   }
-  const int64_t nunits = int64_t(src.size());
-  std::vector<AflParams> prm(nunits);
+  const int64_t nunits = int64_t(usrc.size());
+  in.prm.resize(nunits);
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
   for (int64_t u = 0; u < nunits; ++u) {
     if (afl) {
-      if (!afl_params(src[u].a, src[u].n, src[u].u, &prm[u])) bad |= 1;
+      if (!afl_params(usrc[u], in.unit_len[u], uprec[u], &in.prm[u])) bad |= 1;
     } else {
-      for (int64_t j = 0; j < src[u].n; ++j)
-        if (!std::isfinite(src[u].a[j])) bad |= 1;
-      prm[u] = AflParams{0.0, 0, 0, 64};
+      for (int64_t j = 0; j < in.unit_len[u]; ++j)
+        if (!std::isfinite(usrc[u][j])) bad |= 1;
+      in.prm[u] = AflParams{1.0, 0, 0, 64};
     }
   }
   if (bad) return set_error(HLR_ERR_INVALID, "hlr_upload: NaN or Inf in block data");
-
-  std::vector<uint64_t> uoff(nunits + 1, 0);
+  in.uoff.assign(nunits + 1, 0);
   uint64_t stream_bytes = 0;
   for (int64_t u = 0; u < nunits; ++u) {
-    size_t bytes = afl ? afl_bytes(src[u].n, prm[u].w) : size_t(src[u].n) * 8;
+    size_t bytes = afl_bytes(in.unit_len[u], in.prm[u].w);
     stream_bytes += bytes;
-    uoff[u + 1] = uoff[u] + padded16(bytes);
+    in.uoff[u + 1] = in.uoff[u] + padded16(bytes);
   }
+  HostBuf canon;
+  canon.p = static_cast<uint8_t *>(std::aligned_alloc(64, align_up(in.uoff[nunits] + 64, 64)));
+  if (!canon.p) return set_error(HLR_ERR_OOM, "hlr_upload: host allocation failed");
+  std::memset(canon.p + in.uoff[nunits], 0, 64);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t u = 0; u < nunits; ++u) {
+    uint8_t *dst = canon.p + in.uoff[u];
+    std::memset(dst, 0, in.uoff[u + 1] - in.uoff[u]);
+    if (afl)
+      afl_pack(usrc[u], in.unit_len[u], in.prm[u], dst);
+    else
+      std::memcpy(dst, usrc[u], size_t(in.unit_len[u]) * 8);
+  }
+  in.canon = canon.p;
 
-  // ---- phase-1 items (lowrank blocks), sorted by decreasing cost
-  std::vector<LRBlock> lrb;
-  std::vector<int64_t> lr_of_block(nb, -1);
-  std::vector<P1Item> items;
-  std::vector<double> item_cost;
-  uint32_t tbase = 0, part = 0;
-  for (int64_t b = 0; b < nb; ++b) {
-    const hlr_block_desc &B = d->blocks[b];
-    if (B.kind != HLR_LOWRANK || B.rank == 0) continue;
-    int64_t nch = (B.ncols + kRowsPerItem - 1) / kRowsPerItem;
-    if (nch > 65535) return set_error(HLR_ERR_UNSUPPORTED, "hlr_upload: lowrank block too wide");
-    LRBlock L;
-    L.tbase = tbase;
-    L.part0 = part;
-    L.k = uint16_t(B.rank);
-    L.nchunks = uint16_t(nch);
-    L.xunit0 = uint32_t(blk_unit0[b] + B.rank);
-    lr_of_block[b] = int64_t(lrb.size());
-    double wsum = 0;
-    for (int i = 0; i < B.rank; ++i) wsum += prm[L.xunit0 + i].w;
-    for (int64_t c = 0; c < nch; ++c) {
-      P1Item it;
-      it.blk = uint32_t(lrb.size());
-      it.row0 = uint32_t(c * kRowsPerItem);
-      it.xoff = uint32_t(B.col0 + c * kRowsPerItem);
-      it.nrows = uint16_t(std::min<int64_t>(kRowsPerItem, B.ncols - c * kRowsPerItem));
-      it.chunk = uint16_t(c);
-      items.push_back(it);
-      item_cost.push_back(double(it.nrows) * wsum + 64.0 * B.rank);
-    }
-    lrb.push_back(L);
-    tbase += uint32_t(B.rank);
-    part += uint32_t(nch * B.rank);
-  }
-  {
-    std::vector<int64_t> ord(items.size());
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return item_cost[a] > item_cost[b]; });
-    std::vector<P1Item> s(items.size());
-    for (size_t i = 0; i < ord.size(); ++i) s[i] = items[ord[i]];
-    items.swap(s);
-  }
-
-  // ---- phase-2 owners (leaf row intervals <= 64 rows) and their contributions
-  std::vector<Leaf> leaves;
-  std::vector<Contrib> contribs;
-  std::vector<double> leaf_cost;
-  std::vector<std::vector<Contrib>> per_leaf;
-  for (int64_t i = 0; i < nint; ++i) {
-    std::vector<int64_t> bl = cover[i];
-    std::sort(bl.begin(), bl.end());
-    for (int64_t r0 = brk[i]; r0 < brk[i + 1]; r0 += kLeafRows) {
-      int64_t nr = std::min<int64_t>(kLeafRows, brk[i + 1] - r0);
-      std::vector<Contrib> cs;
-      double cost = 0;
-      uint32_t colbase = 0;
-      for (int64_t b : bl) {
-        const hlr_block_desc &B = d->blocks[b];
-        Contrib c{};
-        c.rowoff = uint32_t(r0 - B.row0);
-        c.colbase = colbase;
-        if (B.kind == HLR_DENSE) {
-          c.kind = CONTRIB_DENSE;
-          c.unit = uint32_t(blk_unit0[b]);
-          c.ncols = uint32_t(B.ncols);
-          c.ld = uint32_t(B.nrows);
-          c.mbase = uint32_t(B.col0);
-          cost += double(nr) * B.ncols * prm[c.unit].w;
-        } else {
-          if (B.rank == 0) continue;
-          c.kind = CONTRIB_LOWRANK;
-          c.unit = uint32_t(blk_unit0[b]);
-          c.ncols = uint32_t(B.rank);
-          c.ld = uint32_t(B.nrows);
-          c.mbase = lrb[lr_of_block[b]].tbase;
-          for (int k = 0; k < B.rank; ++k) cost += double(nr) * prm[c.unit + k].w;
-        }
-        colbase += c.ncols;
-        cs.push_back(c);
-      }
-      Leaf L{uint32_t(r0), uint32_t(nr), 0, 0};
-      leaves.push_back(L);
-      leaf_cost.push_back(cost + 64.0 * cs.size());
-      per_leaf.push_back(std::move(cs));
-    }
-  }
-  {
-    std::vector<int64_t> ord(leaves.size());
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return leaf_cost[a] > leaf_cost[b]; });
-    std::vector<Leaf> s;
-    s.reserve(leaves.size());
-    for (int64_t o : ord) {
-      Leaf L = leaves[o];
-      L.c0 = uint32_t(contribs.size());
-      for (auto &c : per_leaf[o]) contribs.push_back(c);
-      L.c1 = uint32_t(contribs.size());
-      s.push_back(L);
-    }
-    leaves.swap(s);
-  }
+  // ---- work lists
+  in.cover = &cover;
+  in.brk = &brk;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int nct = ctas_per_phase(dev);
+  if (nct <= 0) return set_error(HLR_ERR_CUDA, "hlr_upload: cannot query the device");
+  PackOutput po;
+  const bool want_map = values <= kDecodeMapMaxValues;
+  int rc = pack_work(in, nct, want_map, &po);
+  if (rc) return rc;
 
   // ---- arena layout
   auto H = std::make_unique<Handle>();
-  cudaGetDevice(&H->device);
+  H->device = dev;
   H->format = d->format;
-  size_t off = align_up(uoff[nunits] + 64, 256);
-  size_t o_units = off;
-  off = align_up(off + sizeof(UnitHdr) * nunits, 256);
-  size_t o_sigma = off;
-  off = align_up(off + 8 * size_t(rank_sum), 256);
-  size_t o_lrb = off;
-  off = align_up(off + sizeof(LRBlock) * lrb.size(), 256);
-  size_t o_items = off;
-  off = align_up(off + sizeof(P1Item) * items.size(), 256);
-  size_t o_leaves = off;
-  off = align_up(off + sizeof(Leaf) * leaves.size(), 256);
-  size_t o_contribs = off;
-  off = align_up(off + sizeof(Contrib) * contribs.size(), 256);
-  size_t o_perm = off;
+  size_t off = 0;
+  const size_t o_ph0 = off;
+  off = align_up(off + po.ph[0].bytes.size() + 64, 256);
+  const size_t o_ph1 = off;
+  off = align_up(off + po.ph[1].bytes.size() + 64, 256);
+  // issue streams: per piece one descriptor, then its aux copies (offsets filled in below)
+  std::vector<IssueEnt> ent[2];
+  std::vector<uint32_t> cta_e0[2], cta_np[2];
+  for (int p = 0; p < 2; ++p) {
+    const PhaseOut &ph = po.ph[p];
+    for (int q = 0; q < nct; ++q) {
+      cta_e0[p].push_back(uint32_t(ent[p].size()));
+      cta_np[p].push_back(ph.cta_p0[q + 1] - ph.cta_p0[q]);
+      for (uint32_t k = ph.cta_p0[q]; k < ph.cta_p0[q + 1]; ++k) {
+        uint32_t nel = 0;
+        for (uint32_t a = ph.aux_idx[k]; a < ph.aux_idx[k + 1]; ++a) nel += ph.aux[a].nelem;
+        IssueEnt e{};
+        const uint64_t rel = ph.piece_off[k];  // relative to the region; made absolute below
+        e.a = uint32_t(rel & 0xffffffffu);
+        e.b = uint32_t(rel >> 32) | kIssuePiece;
+        e.c = uint32_t(ph.piece_off[k + 1] - ph.piece_off[k]);
+        e.d = nel;
+        ent[p].push_back(e);
+        for (uint32_t a = ph.aux_idx[k]; a < ph.aux_idx[k + 1]; ++a) {
+          const AuxCopy &c = ph.aux[a];
+          ent[p].push_back(IssueEnt{c.elem0, uint32_t(c.nelem) | (uint32_t(c.which) << 16), c.soff, 0});
+        }
+      }
+    }
+    cta_e0[p].push_back(uint32_t(ent[p].size()));
+  }
+  size_t o_meta[2][3];
+  for (int p = 0; p < 2; ++p) {
+    o_meta[p][0] = off;
+    off = align_up(off + sizeof(IssueEnt) * (ent[p].size() + 32), 256);
+    o_meta[p][1] = off;
+    off = align_up(off + 4 * cta_e0[p].size(), 256);
+    o_meta[p][2] = off;
+    off = align_up(off + 4 * cta_np[p].size(), 256);
+  }
+  const size_t o_fac64 = off;
+  off = align_up(off + 8 * (size_t(rank_sum) + 8), 256);
+  const size_t o_fac32 = off;
+  off = align_up(off + 4 * (size_t(rank_sum) + 8), 256);
+  const size_t o_comb = off;
+  off = align_up(off + sizeof(Combine) * po.comb.size() + 16, 256);
+  const size_t o_perm = off;
   off = align_up(off + 8 * size_t(n), 256);
-  size_t image_bytes = off;  // everything above is copied from the host
-  size_t o_x64 = off;
+  const size_t image_bytes = off;  // everything above is copied from the host
+  const size_t o_x64 = off;
+  off = align_up(off + 8 * (size_t(n) + 8), 256);
+  const size_t o_x32 = off;
+  off = align_up(off + 4 * (size_t(n) + 8), 256);
+  const size_t o_tw64 = off;
+  off = align_up(off + 8 * (size_t(rank_sum) + 8), 256);
+  const size_t o_tw32 = off;
+  off = align_up(off + 4 * (size_t(rank_sum) + 8), 256);
+  const size_t o_part = off;
+  off = align_up(off + 8 * size_t(po.part_total) + 8, 256);
+  const size_t o_status = off;
+  off = align_up(off + 64, 256);
+  const size_t o_xdev = off;
   off = align_up(off + 8 * size_t(n), 256);
-  size_t o_x32 = off;
-  off = align_up(off + 4 * size_t(n), 256);
-  size_t o_t = off;
-  off = align_up(off + 8 * size_t(rank_sum), 256);
-  size_t o_part = off;
-  off = align_up(off + 8 * size_t(part), 256);
-  size_t o_cnt = off;
-  off = align_up(off + 4 * (size_t(lrb.size()) + 8), 256);
-  size_t o_xdev = off;
-  off = align_up(off + 8 * size_t(n), 256);
-  size_t o_ydev = off;
+  const size_t o_ydev = off;
   off = align_up(off + 8 * size_t(n), 256);
   const size_t arena_bytes = off;
-  if ((o_units >> 4) >= (uint64_t(1) << 40)) return set_error(HLR_ERR_UNSUPPORTED, "hlr_upload: arena too large");
 
   HostBuf img;
   img.p = static_cast<uint8_t *>(std::aligned_alloc(256, align_up(image_bytes, 256)));
   if (!img.p) return set_error(HLR_ERR_OOM, "hlr_upload: host staging allocation failed");
   uint8_t *P = img.p;
-  std::memset(P + uoff[nunits], 0, o_units - uoff[nunits]);
-
-  std::vector<UnitHdr> hdr(nunits);
-#pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t u = 0; u < nunits; ++u) {
-    uint8_t *dst = P + uoff[u];
-    std::memset(dst, 0, uoff[u + 1] - uoff[u]);
-    if (afl)
-      afl_pack(src[u].a, src[u].n, prm[u], dst);
-    else
-      std::memcpy(dst, src[u].a, size_t(src[u].n) * 8);
-    UnitHdr h;
-    h.m_min = prm[u].m_min;
-    uint64_t o16 = uoff[u] >> 4;
-    h.off_lo = uint32_t(o16 & 0xffffffffu);
-    h.off_hi = uint8_t(o16 >> 32);
-    h.e = uint8_t(prm[u].e);
-    h.m = uint8_t(prm[u].m);
-    h.w = uint8_t(prm[u].w);
-    hdr[u] = h;
-  }
-  std::memcpy(P + o_units, hdr.data(), sizeof(UnitHdr) * nunits);
-  {
-    double *sg = reinterpret_cast<double *>(P + o_sigma);
-    for (int64_t b = 0; b < nb; ++b) {
-      const hlr_block_desc &B = d->blocks[b];
-      if (lr_of_block[b] < 0) continue;
-      std::memcpy(sg + lrb[lr_of_block[b]].tbase, B.sigma, 8 * size_t(B.rank));
+  std::memset(P, 0, image_bytes);
+  std::memcpy(P + o_ph0, po.ph[0].bytes.data(), po.ph[0].bytes.size());
+  std::memcpy(P + o_ph1, po.ph[1].bytes.data(), po.ph[1].bytes.size());
+  const size_t o_ph[2] = {o_ph0, o_ph1};
+  for (int p = 0; p < 2; ++p) {
+    for (auto &e : ent[p]) {
+      if (!(e.b & kIssuePiece)) continue;
+      const uint64_t abs = ((uint64_t(e.b & ~kIssuePiece) << 32) | e.a) + o_ph[p];
+      e.a = uint32_t(abs & 0xffffffffu);
+      e.b = uint32_t(abs >> 32) | kIssuePiece;
     }
+    if (!ent[p].empty()) std::memcpy(P + o_meta[p][0], ent[p].data(), sizeof(IssueEnt) * ent[p].size());
+    std::memcpy(P + o_meta[p][1], cta_e0[p].data(), 4 * cta_e0[p].size());
+    std::memcpy(P + o_meta[p][2], cta_np[p].data(), 4 * cta_np[p].size());
   }
-  if (!lrb.empty()) std::memcpy(P + o_lrb, lrb.data(), sizeof(LRBlock) * lrb.size());
-  if (!items.empty()) std::memcpy(P + o_items, items.data(), sizeof(P1Item) * items.size());
-  std::memcpy(P + o_leaves, leaves.data(), sizeof(Leaf) * leaves.size());
-  if (!contribs.empty()) std::memcpy(P + o_contribs, contribs.data(), sizeof(Contrib) * contribs.size());
+  if (rank_sum) {
+    std::memcpy(P + o_fac64, po.fac.data(), 8 * po.fac.size());
+    float *f32 = reinterpret_cast<float *>(P + o_fac32);
+    for (size_t i = 0; i < po.fac.size(); ++i) f32[i] = float(po.fac[i]);
+  }
+  if (!po.comb.empty()) std::memcpy(P + o_comb, po.comb.data(), sizeof(Combine) * po.comb.size());
   std::memcpy(P + o_perm, perm.data(), 8 * size_t(n));
 
   void *arena = nullptr;
@@ -395,38 +351,48 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   H->arena_bytes = arena_bytes;
   DevLayout &L = H->L;
   L.base = A;
-  L.units = reinterpret_cast<const UnitHdr *>(A + o_units);
-  L.sigma = reinterpret_cast<const double *>(A + o_sigma);
-  L.lrb = reinterpret_cast<const LRBlock *>(A + o_lrb);
-  L.items = reinterpret_cast<const P1Item *>(A + o_items);
-  L.leaves = reinterpret_cast<const Leaf *>(A + o_leaves);
-  L.contribs = reinterpret_cast<const Contrib *>(A + o_contribs);
   L.perm = reinterpret_cast<const int64_t *>(A + o_perm);
+  L.fac64 = reinterpret_cast<const double *>(A + o_fac64);
+  L.fac32 = reinterpret_cast<const float *>(A + o_fac32);
+  for (int p = 0; p < 2; ++p) {
+    L.ph[p].ent = reinterpret_cast<const IssueEnt *>(A + o_meta[p][0]);
+    L.ph[p].cta_e0 = reinterpret_cast<const uint32_t *>(A + o_meta[p][1]);
+    L.ph[p].cta_np = reinterpret_cast<const uint32_t *>(A + o_meta[p][2]);
+    L.ph[p].nct = nct;
+    L.ph[p].np = int32_t(po.ph[p].piece_off.size()) - 1;
+  }
   L.xperm64 = reinterpret_cast<double *>(A + o_x64);
   L.xperm32 = reinterpret_cast<float *>(A + o_x32);
-  L.t = reinterpret_cast<double *>(A + o_t);
+  L.tw64 = reinterpret_cast<double *>(A + o_tw64);
+  L.tw32 = reinterpret_cast<float *>(A + o_tw32);
   L.partial = reinterpret_cast<double *>(A + o_part);
-  L.counters = reinterpret_cast<uint32_t *>(A + o_cnt);
+  L.comb = reinterpret_cast<const Combine *>(A + o_comb);
+  L.status = reinterpret_cast<uint32_t *>(A + o_status);
   L.xdev = reinterpret_cast<double *>(A + o_xdev);
   L.ydev = reinterpret_cast<double *>(A + o_ydev);
   L.n = n;
-  L.nlr = int32_t(lrb.size());
-  L.nitems = int32_t(items.size());
-  L.nleaves = int32_t(leaves.size());
-  L.format = d->format;
-  H->ncontribs = int64_t(contribs.size());
-  H->part_total = part;
+  L.ncnt = int32_t(po.ncnt);
+  L.raw = afl ? 0 : 1;
   H->nunits = nunits;
   H->values = values;
-  H->scratch_off = o_x64;
-  H->scratch_bytes = arena_bytes - o_x64;
-  H->unit_hdr = hdr;
-  H->unit_len.resize(nunits);
-  H->unit_value_offset.resize(nunits + 1);
-  H->unit_value_offset[0] = 0;
-  for (int64_t u = 0; u < nunits; ++u) {
-    H->unit_len[u] = src[u].n;
-    H->unit_value_offset[u + 1] = H->unit_value_offset[u] + src[u].n;
+  if (want_map) {
+    H->slice_src = std::move(po.slice_src);
+    H->slice_dst = std::move(po.slice_dst);
+    H->slice_n = std::move(po.slice_n);
+    H->slice_unit = std::move(po.slice_unit);
+    for (size_t i = 0; i < H->slice_src.size(); ++i) {
+      const uint64_t v = H->slice_src[i];
+      const uint64_t ph = v >> 63;  // phase tag
+      H->slice_src[i] = (v & ~(uint64_t(1) << 63)) + 8 * uint64_t(ph ? o_ph1 : o_ph0);
+    }
+    H->unit_mmin.resize(nunits);
+    H->unit_e.resize(nunits);
+    H->unit_m.resize(nunits);
+    for (int64_t u = 0; u < nunits; ++u) {
+      H->unit_mmin[u] = in.prm[u].m_min;
+      H->unit_e[u] = uint8_t(in.prm[u].e);
+      H->unit_m[u] = uint8_t(in.prm[u].m);
+    }
   }
 
   hlr_info &I = H->info;
@@ -435,36 +401,34 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   I.ndense = ndense;
   I.nlowrank = nb - ndense;
   I.nunits = nunits;
-  I.nleaves = int64_t(leaves.size());
-  I.nitems = int64_t(items.size());
+  I.nleaves = po.nleaves;
+  I.nitems = po.nitems;
   I.rank_sum = rank_sum;
   I.values = values;
   I.fp64_bytes = uint64_t(values) * 8 + uint64_t(rank_sum) * 8;
   I.stream_bytes = stream_bytes;
-  I.header_bytes = afl ? uint64_t(nunits) * sizeof(UnitHdr) : 0;
+  I.header_bytes = afl ? uint64_t(nunits) * 16 : 0;
   I.algorithmic_bytes = stream_bytes + I.header_bytes + 8 * uint64_t(rank_sum) + 32 * uint64_t(n);
   I.device_bytes = arena_bytes;
   double fl = 0;
+  uint64_t xs = 0, nx = 0;
   for (int64_t b = 0; b < nb; ++b) {
     const hlr_block_desc &B = d->blocks[b];
-    if (B.kind == HLR_DENSE)
+    if (B.kind == HLR_DENSE) {
       fl += 2.0 * double(B.nrows) * double(B.ncols);
-    else
+    } else {
       fl += 2.0 * double(B.rank) * double(B.nrows + B.ncols);
-  }
-  I.flops = fl;
-  {
-    uint64_t xs = 0, nx = 0;
-    for (const auto &L : lrb)
-      for (int i = 0; i < L.k; ++i) {
-        const int64_t u = int64_t(L.xunit0) + i;
-        xs += afl ? afl_bytes(src[u].n, prm[u].w) : uint64_t(src[u].n) * 8;
+      for (int i = 0; i < B.rank; ++i) {
+        const int64_t u = in.blk_unit0[b] + B.rank + i;
+        xs += afl_bytes(in.unit_len[u], in.prm[u].w);
         ++nx;
       }
-    const uint64_t hb = afl ? sizeof(UnitHdr) : 0;
-    I.phase1_bytes = xs + hb * nx + 16 * uint64_t(rank_sum) + 4 * uint64_t(n);
-    I.phase2_bytes = (stream_bytes - xs) + hb * (uint64_t(nunits) - nx) + 8 * uint64_t(rank_sum) + 32 * uint64_t(n);
+    }
   }
+  I.flops = fl;
+  const uint64_t hb = afl ? 16 : 0;
+  I.phase1_bytes = xs + hb * nx + 16 * uint64_t(rank_sum) + 4 * uint64_t(n);
+  I.phase2_bytes = (stream_bytes - xs) + hb * (uint64_t(nunits) - nx) + 8 * uint64_t(rank_sum) + 32 * uint64_t(n);
 
   std::lock_guard<std::mutex> lk(g_mu);
   uint64_t id = g_next++;
@@ -512,10 +476,29 @@ extern "C" int hlr_matvec(hlr_handle h, const double *x, double *y, int flags, v
   return launch_matvec(*H, x, y, flags, stream);
 }
 
+extern "C" int hlr_check(hlr_handle h, void *stream) {
+  Handle *H = lookup(h);
+  if (!H) return set_error(HLR_ERR_INVALID, "hlr_check: unknown handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t s[4] = {0, 0, 0, 0};
+  cudaError_t ce = cudaMemcpyAsync(s, H->L.status, sizeof(s), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string("hlr_check: ") + cudaGetErrorString(ce));
+  if (s[0] | s[1] | s[2] | s[3]) {
+    cudaMemsetAsync(H->L.status, 0, sizeof(s), st);
+    cudaStreamSynchronize(st);
+    return set_error(HLR_ERR_TIMEOUT, "hlr_check: a device-side wait ran out of time (status " +
+                                          std::to_string(s[0]) + ")");
+  }
+  return HLR_OK;
+}
+
 extern "C" int hlr_decode_units(hlr_handle h, double *out, int64_t cap, void *stream) {
   Handle *H = lookup(h);
   if (!H || !out) return set_error(HLR_ERR_INVALID, "hlr_decode_units: unknown handle or null output");
   if (cap < H->values) return set_error(HLR_ERR_INVALID, "hlr_decode_units: output too small");
+  if (H->values > 0 && H->slice_src.empty())
+    return set_error(HLR_ERR_UNSUPPORTED, "hlr_decode_units: only for matrices of at most 2^26 values");
   return launch_decode_units(*H, out, stream);
 }
 

@@ -45,6 +45,7 @@ def _run(A, x, y0, acc):
     xd = torch.from_numpy(x).cuda()
     yd = torch.from_numpy(y0.copy()).cuda()
     A.matvec(xd, yd, acc=acc)
+    A.check()
     torch.cuda.synchronize()
     return yd.cpu().numpy()
 
@@ -92,14 +93,15 @@ def test_deterministic_bits(exp2d_case):
     A.free()
 
 
-def test_wide_codes_eps_1e8():
+def test_wide_codes_eps_1e10():
+    # eps = 1e-10: dense codes have m = 34 > 23 and w > 32 (the FP32 path's generic decoder)
     p = synth.exp2d_problem(1500, seed=3)
-    H = ohm.build_hmatrix(p, 1e-8, method="svd")
+    H = ohm.build_hmatrix(p, 1e-10, method="svd")
     C = ohm.compress(H)
     assert max(u.w for cb in C.blocks for u in cb.units) > 32
     x = synth.rhs(p.n, 1)
     ref = omv.matvec(C, x)
-    A = hg.upload(p.n, H.perm, oracle_blocks(H), 1e-8)
+    A = hg.upload(p.n, H.perm, oracle_blocks(H), 1e-10)
     ap = _abs_product(C, x)
     for acc in ("fp64", "fp32"):
         _check(_run(A, x, np.zeros(p.n), acc), ref, ap, acc)
