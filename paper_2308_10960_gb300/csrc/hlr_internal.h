@@ -27,10 +27,13 @@ namespace hlr {
 
 constexpr int kPieceMax = 16384;  // bytes of one piece (header, segments, column headers, data)
 constexpr int kMaxCols = 128;     // column slices per piece (one per consumer lane)
-constexpr int kAuxMax = 512;      // multiplier elements staged with one piece
-constexpr int kStages = 3;        // ring slots per CTA
+constexpr int kAuxMax1 = 1024;    // phase 1: staged elements per piece (x of the rows, factors)
+constexpr int kAuxMax2 = 512;     // phase 2: staged multipliers per piece
+constexpr int kAuxMax = kAuxMax1; // the larger of the two
+constexpr int kStages = 2;        // ring slots per CTA
 constexpr int kConsumers = 128;   // consumer threads (4 warps) per CTA, plus one producer warp
 constexpr int kRowsPerItem = 256;
+constexpr int kSubRows = 64;      // phase 1: rows of an X column read by one lane
 constexpr int kLeafRows = 64;
 
 enum : uint8_t { SEG_DENSE = 0, SEG_W = 1, SEG_X = 2 };
@@ -177,7 +180,7 @@ int launch_decode_units(const Handle &H, double *out, void *stream);
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out,
                          void *stream_);
 int profile_read(Handle &H, double *ms, int *calls);
-int ctas_per_phase(int device);  // persistent grid size of the product kernels
+int ctas_per_phase(int device, int nct[2]);  // persistent grid sizes of the two product kernels
 
 // Host codec (hlr_codec.cpp).
 int mantissa_bits(double u);

@@ -5,17 +5,20 @@
 //   k_product<FMT, 0> (phase 1): for every lowrank block b and column i,
 //               t_b,i m_min(W_b,i) = sigma_i m_min(X_i) m_min(W_i) sum_r X~code_r,i x_r;
 //               a block wider than 256 rows is split into items whose partial sums are
-//               combined in chunk order by the last one to finish (no spin waits)
+//               written to scratch and summed in chunk order by k_combine
+//   k_combine : deterministic sum of those partial sums, times the column factor
 //   k_product<FMT, 1> (phase 2): per leaf row interval l (<= 64 rows), y|l += the sum over the
-//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma, in one fixed order, one
-//               owner per row (no atomics on y)
+//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma in one fixed order; the CTA
+//               that owns the leaf adds each row's total to y once (one atomicAdd per row, so
+//               the result does not depend on scheduling as long as y starts from one value)
 //
 // Both phases are persistent kernels over the work-ordered piece streams (hlr_internal.h):
 // one producer warp per CTA issues TMA bulk copies (cp.async.bulk) of the next pieces and of
-// their multipliers into a ring of shared-memory slots guarded by mbarriers; in the four
-// consumer warps every lane owns one column slice of the current piece and decodes its codes
-// one after the other from shared memory (a running 64-bit window, so the per-column set-up is
-// paid once per slice). Phase 2 combines the lanes' values row by row with warp shuffles.
+// their multipliers into a ring of shared-memory slots guarded by mbarriers. In the consumer
+// warps of the compressed paths every lane owns one column slice of the current piece (phase 1:
+// a <= 64-row part of an X column; phase 2: a column of the leaf). Phase 2 in FP32 writes the
+// lanes' products of 16 rows to a padded tile per warp and sums it transposed; the FP64 paths
+// let lanes be rows instead (one FP64 fused multiply-add per value, no cross-lane sums).
 // Every wait is bounded (about 2 s of clock cycles), after which the kernel records an error
 // word and returns.
 //
@@ -50,14 +53,17 @@ struct Tr<FMT_AFL32> {
   using A = float;
   static constexpr int esz = 4;
 };
-template <int FMT>
+// ring slot: piece, 16-byte pad, staged multipliers (phase 1 stages more: x of the items' rows)
+template <int FMT, int PH>
 __host__ __device__ constexpr size_t slot_bytes() {
-  return size_t(kPieceMax) + 16 + size_t(kAuxMax) * Tr<FMT>::esz;
+  return size_t(kPieceMax) + 16 + size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz;
 }
-template <int FMT>
+// dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers and the
+// FP32 path its transposition tiles
+template <int FMT, int PH>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return size_t(kStages) * slot_bytes<FMT>() + 2 * kStages * 8 + 2 * kCWarps * 64 * 8 +
-         (FMT == 0 ? size_t(kCWarps) * 32 * 33 * 4 : 0) + 16;
+  return size_t(kStages) * slot_bytes<FMT, PH>() + 2 * kStages * 8 + 16 +
+         (PH == 1 ? 2 * kCWarps * 64 * 8 + (FMT == 0 ? size_t(kCWarps) * 16 * 33 * 4 : 0) : 0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -78,14 +84,16 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
+// try_wait with a suspend-time hint: a waiting warp sleeps (up to ~20 us per try) until the
+// phase completes instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
+      : "r"(smem_u32(b)), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
@@ -139,6 +147,13 @@ __device__ __forceinline__ float dec_f32(uint32_t code, const ColDec &c) {
   return __uint_as_float(__float_as_uint(v) ^ s);
 }
 
+// +-(v - 1) * mult as one fused multiply-add v * s - s with s = +-mult (fast path)
+__device__ __forceinline__ float dec_mul_f32(uint32_t code, const ColDec &c, float mult) {
+  const uint32_t mag = (code & c.em_mask) * c.scale + 0x3F800000u;
+  const float sm = __uint_as_float(__float_as_uint(mult) ^ ((code << c.sshift) & 0x80000000u));
+  return fmaf(__uint_as_float(mag), sm, -sm);
+}
+
 // +-(v - 1) as FP64 (any width)
 __device__ __forceinline__ double dec_f64(uint64_t code, const ColDec &c) {
   const uint32_t em = c.e + c.m;
@@ -148,36 +163,18 @@ __device__ __forceinline__ double dec_f64(uint64_t code, const ColDec &c) {
   return ((code >> em) & 1ull) ? -v : v;
 }
 
+// code (w <= 32) starting at an arbitrary bit of a shared-memory word array
+__device__ __forceinline__ uint32_t code32_at(const uint32_t *p, uint32_t bit) {
+  const uint32_t q = bit >> 5;
+  return __funnelshift_r(p[q], p[q + 1], bit);
+}
+
 // 64-bit window of a shared-memory word array at an arbitrary bit
 __device__ __forceinline__ uint64_t code64_at(const uint32_t *p, uint32_t bit) {
   const uint32_t q = bit >> 5;
   const uint32_t a = p[q], b = p[q + 1], c = p[q + 2];
   return (uint64_t(__funnelshift_r(b, c, bit)) << 32) | __funnelshift_r(a, b, bit);
 }
-
-// Sequential reader of one column slice: codes of width w <= 32 one after the other.
-struct Seq {
-  const uint32_t *p;
-  uint32_t nxt, lo, hi, pos;
-  __device__ __forceinline__ void init(const uint32_t *base, uint32_t bit) {
-    const uint32_t q = bit >> 5;
-    p = base;
-    lo = base[q];
-    hi = base[q + 1];
-    nxt = q + 2;
-    pos = bit & 31u;
-  }
-  __device__ __forceinline__ uint32_t code() const { return __funnelshift_r(lo, hi, pos); }
-  __device__ __forceinline__ void advance(uint32_t w) {
-    pos += w;
-    if (pos >= 32u) {
-      pos -= 32u;
-      lo = hi;
-      hi = p[nxt];
-      ++nxt;
-    }
-  }
-};
 
 // Value r of a slice (FP32 / FP64 accumulation types) for the generic (wide) path.
 template <typename A>
@@ -225,11 +222,11 @@ __global__ void k_permute(const int64_t *__restrict__ perm, int64_t n, const dou
 // ---------------------------------------------------------------------------------------------
 // Producer: TMA bulk copies of the CTA's pieces and their multipliers into the slot ring
 // ---------------------------------------------------------------------------------------------
-template <int FMT>
+template <int FMT, int PH>
 __device__ void producer(const DevLayout &L, const PhaseDev &P, uint32_t e0, uint32_t e1, uint8_t *smem,
                          uint64_t *full, uint64_t *empty) {
   constexpr uint32_t esz = Tr<FMT>::esz;
-  constexpr size_t slot = slot_bytes<FMT>();
+  constexpr size_t slot = slot_bytes<FMT, PH>();
   const int lane = threadIdx.x & 31;
   const uint8_t *xsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.xperm32)
                                          : reinterpret_cast<const uint8_t *>(L.xperm64);
@@ -304,7 +301,7 @@ __device__ __forceinline__ int find_seg(const Seg *segs, int nseg, int c) {
 template <int FMT>
 __device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty) {
   using A = typename Tr<FMT>::A;
-  constexpr size_t slot = slot_bytes<FMT>();
+  constexpr size_t slot = slot_bytes<FMT, 0>();
   const int t = threadIdx.x, lane = t & 31;
   for (uint32_t i = 0; i < np; ++i) {
     const uint32_t s = i % kStages;
@@ -334,8 +331,8 @@ __device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, u
         lead = sub == 0;
         const uint32_t ch = Wd[sg.col_w + j];
         const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
-        const int r0 = sub * 32;
-        const int rc = min(32, int(sg.nr) - r0);  // rows of this lane (may be <= 0)
+        const int r0 = sub * kSubRows;
+        const int rc = min(kSubRows, int(sg.nr) - r0);  // rows of this lane (may be <= 0)
         const A *xr = aux + sg.xs + r0;
         if constexpr (FMT == FMT_RAW64) {
           const double *Dd = reinterpret_cast<const double *>(Dc) + r0;
@@ -344,27 +341,17 @@ __device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, u
         } else {
           const ColDec c = col_dec((ch >> 16) & 0xffu, ch >> 24);
           if (c.narrow) {
-            Seq q;
-            q.init(Dc, uint32_t(r0) * c.w);
+            uint32_t bit = uint32_t(r0) * c.w;
             if constexpr (FMT == FMT_AFL32) {
               if (c.fast32) {
-#pragma unroll 4
-                for (int r = 0; r < rc; ++r) {
-                  dot = fmaf(dec_f32(q.code(), c), xr[r], dot);
-                  q.advance(c.w);
-                }
+#pragma unroll 8
+                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(dec_f32(code32_at(Dc, bit), c), xr[r], dot);
               } else {
-                for (int r = 0; r < rc; ++r) {
-                  dot = fmaf(float(dec_f64(q.code(), c)), xr[r], dot);
-                  q.advance(c.w);
-                }
+                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(float(dec_f64(code32_at(Dc, bit), c)), xr[r], dot);
               }
             } else {
-#pragma unroll 2
-              for (int r = 0; r < rc; ++r) {
-                dot = fma(dec_f64(q.code(), c), xr[r], dot);
-                q.advance(c.w);
-              }
+#pragma unroll 4
+              for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(code32_at(Dc, bit), c), xr[r], dot);
             }
           } else {
             for (int r = 0; r < rc; ++r) dot += dec_at<A>(Dc, uint32_t(r0 + r) * c.w, c) * xr[r];
@@ -372,9 +359,9 @@ __device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, u
         }
       }
     }
-    // the G lanes of a column (an aligned group) sum their 32-row parts in a fixed order
+    // the G lanes of a column (an aligned group) sum their row parts in a fixed order
 #pragma unroll
-    for (uint32_t o = 1; o < 8; o <<= 1) {
+    for (uint32_t o = 1; o < 4; o <<= 1) {
       const A v = __shfl_xor_sync(kFull, dot, o);
       if (o < G) dot += v;
     }
@@ -439,12 +426,12 @@ template <int FMT>
 __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty,
                                double *red, float *tiles, double *__restrict__ y) {
   using A = typename Tr<FMT>::A;
-  constexpr size_t slot = slot_bytes<FMT>();
+  constexpr size_t slot = slot_bytes<FMT, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  Comp32 acc0, acc1;  // rows lane and lane + 32 of the leaf: this warp's columns so far
+  Comp32 acc[4];  // rows lane + 16 k (lanes 0..15) of the leaf: this warp's columns so far
   uint32_t parity = 0;
   int64_t gi = 0;
-  float *tile = tiles + warp * (32 * 33);
+  float *tile = tiles + warp * (16 * 33);
   for (uint32_t i = 0; i < np; ++i) {
     const uint32_t s = i % kStages;
     if (!mbar_wait(&full[s], (i / kStages) & 1)) {
@@ -459,8 +446,8 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
     const int nr = ph->nr;
     const uint32_t flags = ph->flags;
     if (flags & PF_START_LEAF) {
-      acc0.reset();
-      acc1.reset();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k].reset();
       if (t < nr) gi = __ldg(L.perm + ph->row0 + uint32_t(t));
     }
     A mult = A(0);
@@ -470,43 +457,46 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
       slice_setup<FMT>(sg, t - int(sg.cstart), nr, Wd, aux, start, e, m, mult);
     }
     const ColDec c = col_dec(e, m);
-    Seq q;
-    if (c.narrow) q.init(Wd, start);
-    for (int r0 = 0; r0 < nr; r0 += 32) {
-      const int rows = min(32, nr - r0);
-      if (c.fast32) {
-#pragma unroll 4
-        for (int rr = 0; rr < rows; ++rr) {
-          tile[rr * 33 + lane] = dec_f32(q.code(), c) * mult;
-          q.advance(c.w);
-        }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // 16-row chunks (nr <= 64)
+      const int r0 = 16 * k;
+      if (r0 >= nr) break;
+      const int rows = min(16, nr - r0);
+      const uint32_t bit0 = start + uint32_t(r0) * c.w;
+      if (rows == 16 && c.fast32) {
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) tile[rr * 33 + lane] = dec_mul_f32(code32_at(Wd, bit0 + rr * c.w), c, mult);
+      } else if (c.fast32) {
+        for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_mul_f32(code32_at(Wd, bit0 + rr * c.w), c, mult);
       } else if (c.narrow) {
-        for (int rr = 0; rr < rows; ++rr) {
-          tile[rr * 33 + lane] = float(dec_f64(q.code(), c)) * mult;
-          q.advance(c.w);
-        }
+        for (int rr = 0; rr < rows; ++rr)
+          tile[rr * 33 + lane] = float(dec_f64(code32_at(Wd, bit0 + rr * c.w), c)) * mult;
       } else {
         for (int rr = 0; rr < rows; ++rr)
           tile[rr * 33 + lane] = float(dec_f64(code64_at(Wd, start + uint32_t(r0 + rr) * c.w), c)) * mult;
       }
       __syncwarp();
-      if (lane < rows) {
-        float sum = 0.f;
+      // transposed sum: lane l adds row (l & 15) over columns 16 (l >> 4) .. + 15; the two
+      // halves are combined with one shuffle
+      const int row = lane & 15;
+      float sum = 0.f;
+      if (row < rows) {
+        const float *tr = tile + row * 33 + (lane >> 4) * 16;
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) sum += tile[lane * 33 + cc];
-        if (r0 == 0)
-          acc0.add(sum);
-        else
-          acc1.add(sum);
+        for (int cc = 0; cc < 16; ++cc) sum += tr[cc];
       }
+      sum += __shfl_xor_sync(kFull, sum, 16);
+      if (lane < rows) acc[k].add(sum);
       __syncwarp();
     }
     if (flags & PF_END_LEAF) {
       // per-warp row sums; the two halves of red alternate between leaves, so one barrier
       // suffices (a half is rewritten only after the next leaf's barrier)
       double *buf = red + parity * (kCWarps * 64);
-      buf[warp * 64 + lane] = acc0.value();
-      buf[warp * 64 + 32 + lane] = acc1.value();
+      if (lane < 16) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) buf[warp * 64 + 16 * k + lane] = acc[k].value();
+      }
       bar_consumers();
       if (t < nr) {
         double sum = 0.0;
@@ -528,7 +518,7 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
 template <int FMT>
 __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full,
                                     uint64_t *empty, double *red, double *__restrict__ y) {
-  constexpr size_t slot = slot_bytes<FMT>();
+  constexpr size_t slot = slot_bytes<FMT, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double a0 = 0.0, a1 = 0.0;
   uint32_t parity = 0;
@@ -588,7 +578,7 @@ __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *sm
 template <int FMT, int PH>
 __global__ void __launch_bounds__(kThreads) k_product(DevLayout L, double *__restrict__ y) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr size_t slot = slot_bytes<FMT>();
+  constexpr size_t slot = slot_bytes<FMT, PH>();
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
   uint64_t *empty = full + kStages;
   double *red = reinterpret_cast<double *>(empty + kStages);
@@ -606,7 +596,7 @@ __global__ void __launch_bounds__(kThreads) k_product(DevLayout L, double *__res
   __syncthreads();
   if (np == 0) return;
   if (threadIdx.x >= kConsumers) {
-    producer<FMT>(L, P, e0, e1, smem, full, empty);
+    producer<FMT, PH>(L, P, e0, e1, smem, full, empty);
     return;
   }
   if constexpr (PH == 0)
@@ -678,14 +668,14 @@ namespace {
 
 struct DevProps {
   int sms = 0;
-  int occ = 0;
+  int occ[2] = {0, 0};  // resident CTAs per SM of the phase-1 / phase-2 kernels (FP32 path)
 };
 std::mutex g_props_mu;
 DevProps g_props[64];
 
 template <int FMT, int PH>
 void set_smem_attr() {
-  cudaFuncSetAttribute(k_product<FMT, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<FMT>()));
+  cudaFuncSetAttribute(k_product<FMT, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<FMT, PH>()));
 }
 
 const DevProps &props(int dev) {
@@ -702,9 +692,11 @@ const DevProps &props(int dev) {
     set_smem_attr<FMT_AFL64, 1>();
     set_smem_attr<FMT_RAW64, 0>();
     set_smem_attr<FMT_RAW64, 1>();
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_product<FMT_AFL32, 1>, kThreads, smem_bytes<FMT_AFL32>());
-    P.occ = occ < 1 ? 1 : occ;
+    int o0 = 0, o1 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL32, 0>, kThreads, smem_bytes<FMT_AFL32, 0>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL32, 1>, kThreads, smem_bytes<FMT_AFL32, 1>());
+    P.occ[0] = o0 < 1 ? 1 : o0;
+    P.occ[1] = o1 < 1 ? 1 : o1;
     if (cur != dev) cudaSetDevice(cur);
   }
   return P;
@@ -720,10 +712,10 @@ template <int FMT>
 void launch_phases(const Handle &H, double *y, cudaStream_t st, cudaEvent_t *ev) {
   const DevLayout &L = H.L;
   if (ev) cudaEventRecord(ev[1], st);
-  if (L.ph[0].np > 0) k_product<FMT, 0><<<L.ph[0].nct, kThreads, smem_bytes<FMT>(), st>>>(L, y);
+  if (L.ph[0].np > 0) k_product<FMT, 0><<<L.ph[0].nct, kThreads, smem_bytes<FMT, 0>(), st>>>(L, y);
   if (L.ncnt > 0) k_combine<FMT><<<int(std::min<int64_t>((L.ncnt + 255) / 256, 1024)), 256, 0, st>>>(L);
   if (ev) cudaEventRecord(ev[2], st);
-  if (L.ph[1].np > 0) k_product<FMT, 1><<<L.ph[1].nct, kThreads, smem_bytes<FMT>(), st>>>(L, y);
+  if (L.ph[1].np > 0) k_product<FMT, 1><<<L.ph[1].nct, kThreads, smem_bytes<FMT, 1>(), st>>>(L, y);
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -744,10 +736,12 @@ cudaEvent_t *profile_slot(Handle &H, int flags) {
 
 }  // namespace
 
-int ctas_per_phase(int device) {
+int ctas_per_phase(int device, int nct[2]) {
   const DevProps &P = props(device);
   if (P.sms <= 0) return 0;
-  return P.sms * P.occ;
+  nct[0] = P.sms * P.occ[0];
+  nct[1] = P.sms * P.occ[1];
+  return nct[1];
 }
 
 int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream) {

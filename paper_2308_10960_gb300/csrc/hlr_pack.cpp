@@ -70,8 +70,8 @@ struct Frag {  // one CTA's pieces
 
 class Builder {
  public:
-  Builder(const PackInput &in, const std::vector<int64_t> &uvoff, Frag &f, bool want_map)
-      : in_(in), uvoff_(uvoff), f_(f), map_(want_map) {}
+  Builder(const PackInput &in, const std::vector<int64_t> &uvoff, Frag &f, bool want_map, int aux_max)
+      : in_(in), uvoff_(uvoff), f_(f), map_(want_map), aux_max_(aux_max) {}
 
   int w_of(int64_t u) const { return in_.raw ? 64 : in_.prm[u].w; }
 
@@ -97,7 +97,7 @@ class Builder {
         if (j0 + c > B.ncols || ncols_ + c > kMaxCols) break;
         const size_t bytes = 16 + 32 * (segs_.size() + 1) + a16(4 * cols_.size()) +
                              4 * (data_.size() + words_of(uint64_t(c) * nr * w));
-        if (bytes > size_t(kPieceMax) || aux_elems_ + aligned_span(B.col0 + j0, c) > kAuxMax) break;
+        if (bytes > size_t(kPieceMax) || aux_elems_ + aligned_span(B.col0 + j0, c) > aux_max_) break;
         fit = c;
       }
       if (fit == 0) {
@@ -138,10 +138,10 @@ class Builder {
   //  X (phase 1): x of the rows at [xoff, xoff + nr), factors at [L.tbase + i, ...).
   void slices(uint8_t kind, int64_t u0, const LR &L, int64_t nr, int64_t rowoff, int64_t xoff, uint16_t chunk) {
     const int k = L.k;
-    // X: a column of nr rows is read by G = 2^lg lanes of 32 rows each (aligned lane groups)
+    // X: a column of nr rows is read by G = 2^lg lanes of 64 rows each (aligned lane groups)
     int lg = 0;
     if (kind == SEG_X)
-      while ((32 << lg) < nr) ++lg;
+      while ((kSubRows << lg) < nr) ++lg;
     const uint32_t G = 1u << lg;
     int i0 = 0;
     while (i0 < k) {
@@ -158,7 +158,7 @@ class Builder {
           need += aligned_span(xoff, nr) + aligned_span(L.tbase + i0, c);
         else
           need += aligned_span(L.tbase + i0, c);
-        if (bytes > size_t(kPieceMax) || need > kAuxMax) break;
+        if (bytes > size_t(kPieceMax) || need > aux_max_) break;
         wsum += wi;
         fit = c;
       }
@@ -278,6 +278,7 @@ class Builder {
   const std::vector<int64_t> &uvoff_;
   Frag &f_;
   bool map_;
+  int aux_max_;
   uint16_t leaf_nr_ = 0;
   uint32_t leaf_row0_ = 0;
   bool leaf_start_ = false;
@@ -336,7 +337,7 @@ void concat(std::vector<Frag> &frags, PhaseOut &po, bool phase2, PackOutput *out
 
 }  // namespace
 
-int pack_work(const PackInput &in, int nct, bool want_map, PackOutput *out) {
+int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput *out) {
   const int64_t nb = in.nblocks;
   const int64_t nunits = int64_t(in.unit_len.size());
   std::vector<int64_t> uvoff(nunits + 1, 0);
@@ -424,11 +425,12 @@ int pack_work(const PackInput &in, int nct, bool want_map, PackOutput *out) {
 
   // ---- phase 1 (items)
   {
+    const int nct = nct2[0];
     auto per = assign(items, nct);
     std::vector<Frag> frags(nct);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < nct; ++q) {
-      Builder bld(in, uvoff, frags[q], want_map);
+      Builder bld(in, uvoff, frags[q], want_map, kAuxMax1);
       for (int64_t t : per[q]) {
         const Task &T = items[t];
         const int64_t b = T.a;
@@ -442,11 +444,12 @@ int pack_work(const PackInput &in, int nct, bool want_map, PackOutput *out) {
   }
   // ---- phase 2 (leaves)
   {
+    const int nct = nct2[1];
     auto per = assign(leaves, nct);
     std::vector<Frag> frags(nct);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < nct; ++q) {
-      Builder bld(in, uvoff, frags[q], want_map);
+      Builder bld(in, uvoff, frags[q], want_map, kAuxMax2);
       for (int64_t t : per[q]) {
         const Task &T = leaves[t];
         std::vector<int64_t> bl = cover[T.a];

@@ -43,7 +43,7 @@ struct PackOutput {
   std::vector<uint32_t> slice_unit;
 };
 
-// Build both phases' piece streams for `nct` CTAs. Returns HLR_OK or an HLR_ERR_* code.
-int pack_work(const PackInput &in, int nct, bool want_map, PackOutput *out);
+// Build both phases' piece streams for nct[0] (phase 1) and nct[1] (phase 2) CTAs. Returns HLR_OK or an HLR_ERR_* code.
+int pack_work(const PackInput &in, const int nct[2], bool want_map, PackOutput *out);
 
 }  // namespace hlr

@@ -227,8 +227,8 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   in.brk = &brk;
   int dev = 0;
   cudaGetDevice(&dev);
-  const int nct = ctas_per_phase(dev);
-  if (nct <= 0) return set_error(HLR_ERR_CUDA, "hlr_upload: cannot query the device");
+  int nct[2] = {0, 0};
+  if (ctas_per_phase(dev, nct) <= 0) return set_error(HLR_ERR_CUDA, "hlr_upload: cannot query the device");
   PackOutput po;
   const bool want_map = values <= kDecodeMapMaxValues;
   int rc = pack_work(in, nct, want_map, &po);
@@ -248,7 +248,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   std::vector<uint32_t> cta_e0[2], cta_np[2];
   for (int p = 0; p < 2; ++p) {
     const PhaseOut &ph = po.ph[p];
-    for (int q = 0; q < nct; ++q) {
+    for (int q = 0; q < nct[p]; ++q) {
       cta_e0[p].push_back(uint32_t(ent[p].size()));
       cta_np[p].push_back(ph.cta_p0[q + 1] - ph.cta_p0[q]);
       for (uint32_t k = ph.cta_p0[q]; k < ph.cta_p0[q + 1]; ++k) {
@@ -358,7 +358,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     L.ph[p].ent = reinterpret_cast<const IssueEnt *>(A + o_meta[p][0]);
     L.ph[p].cta_e0 = reinterpret_cast<const uint32_t *>(A + o_meta[p][1]);
     L.ph[p].cta_np = reinterpret_cast<const uint32_t *>(A + o_meta[p][2]);
-    L.ph[p].nct = nct;
+    L.ph[p].nct = nct[p];
     L.ph[p].np = int32_t(po.ph[p].piece_off.size()) - 1;
   }
   L.xperm64 = reinterpret_cast<double *>(A + o_x64);
