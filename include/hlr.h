@@ -178,6 +178,26 @@ int hlr_afl_decode_device(const uint8_t *stream_dev, int64_t n, double m_min, in
  * device map and synchronises cuda_stream. */
 int hlr_decode_units(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stream);
 
+/* The paper has no counterpart of this call: it is hlr_decode_units for callers that must not
+ * allocate device memory, e.g. code running under an allocator that owns all of the GPU's
+ * memory, or code that must not stall other streams (cudaFree synchronises the whole device).
+ * Same arguments, result and limits as hlr_decode_units, but it calls no cudaMalloc, cudaFree
+ * or other allocating routine and does not synchronise: the slice map is copied from host
+ * memory (cudaMemcpyAsync on cuda_stream) into a fixed 4 MiB device array of this library,
+ * which every GPU that loads the library holds until the process exits, and the decoding
+ * kernel reads it from there. The map takes 24 bytes per column slice plus 10 per unit
+ * (each of its seven parts rounded up to 256 bytes); a matrix whose map does not fit is
+ * rejected with HLR_ERR_UNSUPPORTED and a message giving the bytes it needs.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * All calls share the one array and it keeps the last call's map: every call rewrites all of
+ * the map it reads before its kernel runs, so nothing has to start at zero, but calls whose
+ * copies or kernels overlap on the GPU (different streams or threads without ordering between
+ * them) race and may decode with another call's map. Calls on one stream are ordered.
+ * Errors: HLR_ERR_INVALID (unknown handle, null or small output), HLR_ERR_UNSUPPORTED (map
+ * above 4 MiB, more than 2^26 values, device index above 63), HLR_ERR_CUDA. */
+int hlr_decode_units_static(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stream);
+
 /* ---- construction of kernel matrices (host, multithreaded) --------------------------------- */
 #define HLR_KERNEL_EXP      1  /* exp(-|x-y| / scale) + diag * [i == j]                           */
 #define HLR_KERNEL_LAPLACE  2  /* 1 / (4 pi |x-y|) for i != j, diag for i == j                     */

@@ -150,6 +150,14 @@ class DeviceHMatrix:
         B.check(B.lib.hlr_decode_units(C.c_uint64(self.handle), _dev_ptr(out), out.numel(), _stream_ptr(None)))
         return out
 
+    def decode_units_static(self, out, stream=None):
+        """decode_units for callers that cannot allocate device memory: the slice map goes to a
+        fixed 4 MiB array of the library (no allocation, no synchronisation; calls that overlap
+        on the GPU race)."""
+        B.check(B.lib.hlr_decode_units_static(C.c_uint64(self.handle), _dev_ptr(out), out.numel(),
+                                              _stream_ptr(stream)))
+        return out
+
     def check(self, stream=None):
         """Wait for the stream; raise HlrError(HLR_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
         B.check(B.lib.hlr_check(C.c_uint64(self.handle), _stream_ptr(stream)))

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("hlr_afl_decode_device", C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
                                         C.c_void_p]),
     ("hlr_decode_units", C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("hlr_decode_units_static", C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
     ("hlr_build", C.c_int, [C.POINTER(KernelProblem), C.POINTER(C.c_void_p)]),
     ("hlr_host_describe", C.c_int, [C.c_void_p, C.POINTER(HMatrixDesc)]),
     ("hlr_host_free", None, [C.c_void_p]),

@@ -814,6 +814,86 @@ int launch_decode_units(const Handle &H, double *out, void *stream) {
   return rc;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Unit decoding without any allocation (hlr_decode_units_static): the slice map is staged in a
+// fixed array of this library instead of a temporary device allocation.
+// ---------------------------------------------------------------------------------------------
+
+// Every device on which the library's kernels are loaded holds these 4 MiB until the process
+// exits. All calls share them, so two calls whose work overlaps on the GPU race.
+constexpr size_t kStaticScratchBytes = size_t(4) << 20;
+static __device__ __align__(256) uint8_t g_static_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void *g_static_ptr[64] = {};
+
+// Device address of g_static_scratch on `dev`, looked up once per device with that device current.
+int static_scratch(int dev, uint8_t **p) {
+  if (dev < 0 || dev >= 64) return set_error(HLR_ERR_UNSUPPORTED, "hlr_decode_units_static: device index above 63");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return cuda_status("hlr_decode_units_static: cudaGetDevice");
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return cuda_status("hlr_decode_units_static: cudaSetDevice");
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_static_scratch);
+    if (cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return set_error(HLR_ERR_CUDA, std::string("hlr_decode_units_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    }
+    g_static_ptr[dev] = ptr;
+  }
+  *p = static_cast<uint8_t *>(g_static_ptr[dev]);
+  return HLR_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+int launch_decode_units_static(const Handle &H, double *out, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  const int64_t ns = int64_t(H.slice_src.size());
+  const int64_t nu = H.nunits;
+  // map layout in the scratch: src, dst [ns] u64 | m_min [nu] f64 | n, unit [ns] u32 | e, m [nu] u8
+  const size_t o_dst = align256(8 * size_t(ns));
+  const size_t o_mmin = o_dst + align256(8 * size_t(ns));
+  const size_t o_n = o_mmin + align256(8 * size_t(nu));
+  const size_t o_unit = o_n + align256(4 * size_t(ns));
+  const size_t o_e = o_unit + align256(4 * size_t(ns));
+  const size_t o_m = o_e + align256(size_t(nu));
+  const size_t total = o_m + align256(size_t(nu));
+  if (total > kStaticScratchBytes)
+    return set_error(HLR_ERR_UNSUPPORTED, "hlr_decode_units_static: the slice map of this matrix needs " +
+                                              std::to_string(total) + " bytes, more than the " +
+                                              std::to_string(kStaticScratchBytes) +
+                                              " bytes of static scratch (use hlr_decode_units)");
+  uint8_t *base = nullptr;
+  if (int rc = static_scratch(H.device, &base)) return rc;
+  if (ns == 0) return HLR_OK;
+  struct Cp {
+    size_t off;
+    const void *src;
+    size_t bytes;
+  } cps[] = {{0, H.slice_src.data(), 8 * size_t(ns)},        {o_dst, H.slice_dst.data(), 8 * size_t(ns)},
+             {o_mmin, H.unit_mmin.data(), 8 * size_t(nu)},   {o_n, H.slice_n.data(), 4 * size_t(ns)},
+             {o_unit, H.slice_unit.data(), 4 * size_t(ns)},  {o_e, H.unit_e.data(), size_t(nu)},
+             {o_m, H.unit_m.data(), size_t(nu)}};
+  for (const Cp &c : cps)
+    if (c.bytes && cudaMemcpyAsync(base + c.off, c.src, c.bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return cuda_status("hlr_decode_units_static: map copy");
+  const int grid = int(std::min<int64_t>(ns, 65535));
+  k_decode_slices<<<grid, 64, 0, st>>>(H.L.base, reinterpret_cast<const uint64_t *>(base),
+                                       reinterpret_cast<const uint64_t *>(base + o_dst),
+                                       reinterpret_cast<const uint32_t *>(base + o_n),
+                                       reinterpret_cast<const uint32_t *>(base + o_unit),
+                                       reinterpret_cast<const double *>(base + o_mmin), base + o_e, base + o_m, ns,
+                                       H.L.raw, out);
+  return cuda_status("hlr_decode_units_static");
+}
+
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out, void *stream_) {
   cudaStream_t st = static_cast<cudaStream_t>(stream_);
   cudaGetLastError();
@@ -823,3 +903,13 @@ int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, 
 }
 
 }  // namespace hlr
+
+extern "C" int hlr_decode_units_static(hlr_handle h, double *out, int64_t cap, void *stream) {
+  using namespace hlr;
+  Handle *H = lookup(h);
+  if (!H || !out) return set_error(HLR_ERR_INVALID, "hlr_decode_units_static: unknown handle or null output");
+  if (cap < H->values) return set_error(HLR_ERR_INVALID, "hlr_decode_units_static: output too small");
+  if (H->values > 0 && H->slice_src.empty())
+    return set_error(HLR_ERR_UNSUPPORTED, "hlr_decode_units_static: only for matrices of at most 2^26 values");
+  return launch_decode_units_static(*H, out, stream);
+}
