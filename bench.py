@@ -388,7 +388,7 @@ def run_ours(args, world: int, rank: int, local: int):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, world),
                "pct_hbm_peak": value / world / peaks["hbm_gbs"], "pct_hbm_8tbs_spec": value / world / 8000.0,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-               "gpu_launches": 3 * args.steps,
+               "gpu_launches": int(info["launches"]) * args.steps,
                "matrix": {"nblocks": info["nblocks"], "rank_sum": info["rank_sum"],
                           "compressed_bytes": info["stream_bytes"] + info["header_bytes"] + 8 * info["rank_sum"],
                           "fp64_bytes": info["fp64_bytes"],

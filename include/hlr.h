@@ -98,6 +98,8 @@ typedef struct {
                                  singular value (Sigma read, t written) + 4n (x, once)        */
   uint64_t phase2_bytes;      /* phase 2: W and dense streams + their headers + 8 per singular
                                  value (t) + 8n (x, once) + 16n (y) + 8n (perm)              */
+  int64_t launches;           /* kernels one hlr_matvec launches (permute, phase 1, combine of
+                                 split blocks, phase 2; a phase without work is not launched) */
 } hlr_info;
 
 /* Encode the matrix (AFL-APLR or FP64), build the work lists of the product (blocks grouped by

@@ -58,7 +58,8 @@ class Info(C.Structure):
                 ("nunits", C.c_int64), ("nleaves", C.c_int64), ("nitems", C.c_int64), ("rank_sum", C.c_int64),
                 ("values", C.c_int64), ("fp64_bytes", C.c_uint64), ("stream_bytes", C.c_uint64),
                 ("header_bytes", C.c_uint64), ("algorithmic_bytes", C.c_uint64), ("device_bytes", C.c_uint64),
-                ("flops", C.c_double), ("phase1_bytes", C.c_uint64), ("phase2_bytes", C.c_uint64)]
+                ("flops", C.c_double), ("phase1_bytes", C.c_uint64), ("phase2_bytes", C.c_uint64),
+                ("launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -8,9 +8,9 @@
 //               written to scratch and summed in chunk order by k_combine
 //   k_combine : deterministic sum of those partial sums, times the column factor
 //   k_product<FMT, 1> (phase 2): per leaf row interval l (<= 64 rows), y|l += the sum over the
-//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma in one fixed order; the CTA
-//               that owns the leaf adds each row's total to y once (one atomicAdd per row, so
-//               the result does not depend on scheduling as long as y starts from one value)
+//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma in one fixed order; the one
+//               CTA that owns the leaf reads each row of y when the leaf starts and writes
+//               y + (row total) when it ends: no atomics on y, a deterministic result
 //
 // Both phases are persistent kernels over the work-ordered piece streams (hlr_internal.h):
 // one producer warp per CTA issues TMA bulk copies (cp.async.bulk) of the next pieces and of
@@ -431,6 +431,7 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
   Comp32 acc[4];  // rows lane + 16 k (lanes 0..15) of the leaf: this warp's columns so far
   uint32_t parity = 0;
   int64_t gi = 0;
+  double yold = 0.0;  // y of this thread's row, read when the leaf starts
   float *tile = tiles + warp * (16 * 33);
   for (uint32_t i = 0; i < np; ++i) {
     const uint32_t s = i % kStages;
@@ -448,7 +449,10 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
     if (flags & PF_START_LEAF) {
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[k].reset();
-      if (t < nr) gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+      if (t < nr) {
+        gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+        yold = y[gi];
+      }
     }
     A mult = A(0);
     uint32_t start = 0, e = 0, m = 0;
@@ -502,7 +506,7 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
         double sum = 0.0;
 #pragma unroll
         for (int w = 0; w < kCWarps; ++w) sum += buf[w * 64 + t];
-        atomicAdd(y + gi, sum);  // the only update of this row: a fire-and-forget reduction
+        y[gi] = yold + sum;  // the only update of this row (its leaf has one owner CTA)
       }
       parity ^= 1u;
     }
@@ -523,6 +527,7 @@ __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *sm
   double a0 = 0.0, a1 = 0.0;
   uint32_t parity = 0;
   int64_t gi = 0;
+  double yold = 0.0;  // y of this thread's row, read when the leaf starts
   for (uint32_t i = 0; i < np; ++i) {
     const uint32_t s = i % kStages;
     if (!mbar_wait(&full[s], (i / kStages) & 1)) {
@@ -538,7 +543,10 @@ __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *sm
     const uint32_t flags = ph->flags;
     if (flags & PF_START_LEAF) {
       a0 = a1 = 0.0;
-      if (t < nr) gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+      if (t < nr) {
+        gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+        yold = y[gi];
+      }
     }
     const bool ok0 = lane < nr, ok1 = lane + 32 < nr;
     const int ncols = ph->ncols;
@@ -566,7 +574,7 @@ __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *sm
         double sum = 0.0;
 #pragma unroll
         for (int w = 0; w < kCWarps; ++w) sum += buf[w * 64 + t];
-        atomicAdd(y + gi, sum);
+        y[gi] = yold + sum;
       }
       parity ^= 1u;
     }

@@ -428,6 +428,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   I.flops = fl;
   const uint64_t hb = afl ? 16 : 0;
   I.phase1_bytes = xs + hb * nx + 16 * uint64_t(rank_sum) + 4 * uint64_t(n);
+  I.launches = 1 + (po.ph[0].piece_off.size() > 1) + (po.ncnt > 0) + (po.ph[1].piece_off.size() > 1);
   I.phase2_bytes = (stream_bytes - xs) + hb * (uint64_t(nunits) - nx) + 8 * uint64_t(rank_sum) + 32 * uint64_t(n);
 
   std::lock_guard<std::mutex> lk(g_mu);
