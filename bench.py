@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--n", type=int, default=262144)
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip the FP64/plain comparison legs")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS comparison legs")
+    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48"],
+                    help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
+                         "uneven size with 1/8/32 right-hand sides in one batched launch sequence")
     return ap.parse_args()
 
 
@@ -162,6 +165,12 @@ def recorded_traffic(kernel: str) -> dict | None:
     if not e or e.get("source_sha256_16") != h:
         return None
     return e
+
+
+def multi_rhs_bytes(info: dict, n: int, r: int) -> float:
+    """Algorithmic bytes of Y += A~ X with r columns: the compressed streams, headers and Sigma
+    once, the permutation once, and 8n (x) + 16n (y read and write) per column."""
+    return float(info["algorithmic_bytes"]) - 32.0 * n + 8.0 * n + r * 24.0 * n
 
 
 # ------------------------------------------------------------------------------------------
@@ -353,7 +362,24 @@ def run_ours(args, world: int, rank: int, local: int):
         t32 = el / args.steps
         t64 = el64 / steps_cmp
         tp = elp / steps_cmp
+        multi = {}
+        for r in (8, 32):
+            X = torch.from_numpy(synth.rhs(args.n * r, 2 + r)).to(dev).view(r, args.n)
+            Y = torch.zeros((r, args.n), dtype=torch.float64, device=dev)
+
+            def stepm():
+                hg.matvec_batched([A], [X], [Y], acc="fp32", stream=stream)
+            for _ in range(3):
+                stepm()
+            km = max(10, steps_cmp // 8)
+            tm = time_loop(stepm, km, stream) / km
+            bm = multi_rhs_bytes(info, args.n, r)
+            multi[str(r)] = {"ms_per_step": tm * 1e3, "GB/s": bm / tm / 1e9, "algorithmic_bytes": bm,
+                             "speedup_vs_r_single_products": r * t32 / tm}
+            del X, Y
+        A.check()
         extra = {
+            "multi_rhs": multi,
             "afl_fp64_acc": {"ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9},
             "plain_fp64": {"ms_per_step": tp * 1e3, "GB/s": infp["algorithmic_bytes"] / tp / 1e9,
                            "algorithmic_bytes": infp["algorithmic_bytes"],
@@ -401,6 +427,83 @@ def run_ours(args, world: int, rank: int, local: int):
     Hh.free()
 
 
+def run_batch(args, world: int, rank: int, local: int):
+    """48 Matern matrices (n log-uniform in [8192, 131072], seed 3; points seed 100 + i), eps from
+    --eps, right-hand-side counts from {1, 8, 32} (seed 4), X ~ N(0,1): every step is ONE
+    hlr_matvec_batched call over all 48 requests, replayed from a captured CUDA graph.
+    value = sum of the requests' algorithmic bytes / time."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = synth.batch_sizes(48)
+    nrhs = synth.batch_nrhs(48)
+    t0 = time.perf_counter()
+    mats, Xs, Ys, bytes_step, rhs_single = [], [], [], 0.0, 0.0
+    for i, (n, r) in enumerate(zip(sizes, nrhs)):
+        p = synth.matern_problem(n, seed=100 + i)
+        Hh = hg.build_kernel_hmatrix(p.points, "matern15", args.eps, scale=p.params["scale"], diag=p.params["diag"])
+        A = Hh.upload("afl")
+        Hh.free()
+        mats.append(A)
+        Xs.append(torch.from_numpy(synth.rhs(n * r, 1000 + i)).to(dev).view(r, n) if r > 1
+                  else torch.from_numpy(synth.rhs(n, 1000 + i)).to(dev))
+        Ys.append(torch.zeros_like(Xs[-1]))
+        bytes_step += multi_rhs_bytes(A.info, n, r) if r > 1 else float(A.info["algorithmic_bytes"])
+    t_build = time.perf_counter() - t0
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            hg.matvec_batched(mats, Xs, Ys, acc="fp32", stream=stream)
+    torch.cuda.synchronize()
+    eager_el = time_loop(lambda: hg.matvec_batched(mats, Xs, Ys, acc="fp32", stream=stream), args.steps, stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        hg.matvec_batched(mats, Xs, Ys, acc="fp32")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(world)
+    def replay():
+        with torch.cuda.stream(stream):
+            g.replay()
+    el = time_loop(replay, args.steps, stream)
+    barrier(world)
+    clk = clocks.stop()
+    for A in mats:
+        A.check()
+    el_max, total = aggregate(el, bytes_step * args.steps, world)
+    peaks = measured_peaks()
+    if rank == 0:
+        value = total / el_max / 1e9
+        # kernels per batched call: per class (single-RHS FP32, multi-RHS passes) and group of
+        # <= 64 products: permute, phase 1, combine, phase 2
+        n_single = sum(1 for r in nrhs if r == 1)
+        n_pass = sum((r + 7) // 8 for r in nrhs if r > 1)
+        groups = (n_single + 63) // 64 + (n_pass + 63) // 64
+        launches = 4 * groups
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"batch of 48 Matern nu=1.5 matrices, n log-uniform [8192, 131072], "
+                                      f"eps={args.eps:g}, 1/8/32 RHS, one batched call per step (CUDA graph)",
+                          "sizes": sizes, "nrhs": nrhs, "single_rhs_requests": n_single, "rhs_passes": n_pass,
+                          "l2": "inputs larger than L2", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+               "pct_hbm_peak": value / world / peaks["hbm_gbs"],
+               "eager_ms_per_step": eager_el / args.steps * 1e3,
+               "algorithmic_bytes_per_step": bytes_step, "build_s": t_build, "clocks": clk,
+               "gpu_launches": launches * args.steps}
+        print(json.dumps(out), flush=True)
+    for A in mats:
+        A.free()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -416,7 +519,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    run_ours(args, world, rank, local)
+    if args.workload == "batch48":
+        run_batch(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

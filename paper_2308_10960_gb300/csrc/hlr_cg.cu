@@ -194,12 +194,7 @@ extern "C" int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *
     if (nrhs[q] < 0 || (nrhs[q] > 0 && (!X[q] || !Y[q])) || ldx[q] < H->L.n || ldy[q] < H->L.n)
       return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad request " + std::to_string(q));
   }
-  for (int q = 0; q < nreq; ++q) {
-    Handle *H = lookup(h[q]);
-    for (int j = 0; j < nrhs[q]; ++j) {
-      int rc = launch_matvec(*H, X[q] + ldx[q] * j, Y[q] + ldy[q] * j, flags, stream);
-      if (rc) return rc;
-    }
-  }
-  return HLR_OK;
+  std::vector<Handle *> hs(nreq);
+  for (int q = 0; q < nreq; ++q) hs[q] = lookup(h[q]);
+  return launch_batch(nreq, hs.data(), nrhs, X, ldx, Y, ldy, flags, stream);
 }

@@ -70,7 +70,8 @@ struct Seg {
   uint16_t col_w;    // W/X: column headers, words from the piece start; dense: e | m << 8
   uint16_t fs;       // X: aux offset of the first column factor
   uint32_t tidx;     // X: t index of the segment's first column
-  uint32_t cnt;      // unused
+  uint32_t gx;       // global index of the first multiplier: x column (dense), t index (W),
+                     // x row of row 0 of the item (X); read by the multi-RHS kernels
   union {
     double m_min;    // dense: m_min of the block's unit
     struct {
@@ -165,6 +166,9 @@ struct Handle {
   std::vector<double> unit_mmin;     // per unit: m_min
   std::vector<uint8_t> unit_e, unit_m;
   void *cg_ws = nullptr;             // CG work vectors (allocated on first solve)
+  void *multi_ws = nullptr;          // multi-RHS pass scratch (allocated on first use)
+  int multi_passes = 0;              // passes multi_ws holds
+  int64_t part_total = 0;            // phase-1 chunk partial sums of one product
   std::vector<void *> prof_ev;       // cudaEvent_t ring: 4 per profiled product
   int prof_n = 0;
 };
@@ -176,6 +180,9 @@ Handle *lookup(hlr_handle h);
 
 // Kernel side (hlr_kernels.cu).
 int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream);
+// Products of many handles (hlr_matvec_batched); arguments validated by the caller.
+int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *const *X, const int64_t *ldx,
+                 double *const *Y, const int64_t *ldy, int flags, void *stream);
 int launch_decode_units(const Handle &H, double *out, void *stream);
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out,
                          void *stream_);

@@ -53,17 +53,45 @@ struct Tr<FMT_AFL32> {
   using A = float;
   static constexpr int esz = 4;
 };
-// ring slot: piece, 16-byte pad, staged multipliers (phase 1 stages more: x of the items' rows)
-template <int FMT, int PH>
+constexpr int kRB = 8;          // right-hand sides per pass of the multi-RHS product
+constexpr int kMaxBatch = 64;   // products per launch of the batched path
+
+// One product of a launch. Single right-hand side (R = 1): y += A~ x with the handle's scratch.
+// Multi-RHS pass (R = kRB): Y(:, 0:nrhs) += A~ X(:, 0:nrhs) for nrhs <= kRB columns, with the
+// pass's own scratch (xp, tw, part).
+struct Job {
+  DevLayout L;
+  const double *x;   // x (R = 1) or the pass's first column of X (column-major, leading dim ldx)
+  double *y;         // y (R = 1) or the pass's first column of Y (leading dim ldy)
+  int64_t ldx, ldy;
+  int32_t nrhs, pad;
+  float *xp;         // R = kRB: X in cluster order, kRB floats per row      [n + 8][kRB]
+  float *tw;         // R = kRB: t m_min(W), kRB per lowrank column          [rank_sum + 8][kRB]
+  double *part;      // R = kRB: phase-1 chunk partial sums, kRB per entry   [part_total + 1][kRB]
+};
+// A launch's products, passed by value as a kernel parameter (no device-side descriptor copy,
+// so a batched launch needs no allocation and can be captured in a graph).
+template <int NB>
+struct Jobs {
+  int32_t n, pad;
+  Job j[NB];
+};
+static_assert(sizeof(Jobs<kMaxBatch>) < 30000, "kernel parameter size");
+
+// ring slot: piece, 16-byte pad, staged multipliers (phase 1 stages more: x of the items' rows);
+// the multi-RHS kernels read their multipliers from global memory and stage none
+template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t slot_bytes() {
-  return size_t(kPieceMax) + 16 + size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz;
+  return size_t(kPieceMax) + 16 + (R == 1 ? size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz : 0);
 }
 // dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers and the
-// FP32 path its transposition tiles
-template <int FMT, int PH>
+// FP32 path its transposition tiles (multi-RHS: one buffer of kRB sums per row and warp)
+template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return size_t(kStages) * slot_bytes<FMT, PH>() + 2 * kStages * 8 + 16 +
-         (PH == 1 ? 2 * kCWarps * 64 * 8 + (FMT == 0 ? size_t(kCWarps) * 16 * 33 * 4 : 0) : 0);
+  return size_t(kStages) * slot_bytes<FMT, PH, R>() + 2 * kStages * 8 + 16 +
+         (PH == 0 ? 0
+          : R > 1 ? size_t(kCWarps) * 64 * kRB * 8 + size_t(kCWarps) * 32 * kRB * 4
+                  : 2 * kCWarps * 64 * 8 + (FMT == 0 ? size_t(kCWarps) * 16 * 33 * 4 : 0));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -210,23 +238,46 @@ struct Sum64 {
   __device__ __forceinline__ void reset() { s = 0.0; }
 };
 
-__global__ void k_permute(const int64_t *__restrict__ perm, int64_t n, const double *__restrict__ x,
-                          double *__restrict__ x64, float *__restrict__ x32) {
-  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x) {
-    const double v = __ldg(x + __ldg(perm + p));
-    x64[p] = v;
-    x32[p] = float(v);
+// x_perm = x[perm] in FP64 and FP32 for every single-RHS product of the launch (blockIdx.y)
+template <int NB>
+__global__ void k_permute(const __grid_constant__ Jobs<NB> J) {
+  const Job &jb = J.j[blockIdx.y];
+  const DevLayout &L = jb.L;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < L.n; p += int64_t(gridDim.x) * blockDim.x) {
+    const double v = __ldg(jb.x + __ldg(L.perm + p));
+    L.xperm64[p] = v;
+    L.xperm32[p] = float(v);
+  }
+}
+
+// X_perm for a multi-RHS pass: row p holds X(perm[p], 0:kRB) in FP32, zero beyond nrhs
+template <int NB>
+__global__ void k_permute_multi(const __grid_constant__ Jobs<NB> J) {
+  const Job &jb = J.j[blockIdx.y];
+  const DevLayout &L = jb.L;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < L.n; p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = __ldg(L.perm + p);
+    float v[kRB];
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) v[q] = q < jb.nrhs ? float(__ldg(jb.x + q * jb.ldx + g)) : 0.f;
+    float4 *dst = reinterpret_cast<float4 *>(jb.xp + p * kRB);
+#pragma unroll
+    for (int q = 0; q < kRB / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
 }
 
 // ---------------------------------------------------------------------------------------------
 // Producer: TMA bulk copies of the CTA's pieces and their multipliers into the slot ring
 // ---------------------------------------------------------------------------------------------
-template <int FMT, int PH>
-__device__ void producer(const DevLayout &L, const PhaseDev &P, uint32_t e0, uint32_t e1, uint8_t *smem,
-                         uint64_t *full, uint64_t *empty) {
+// Issue the TMA copies of one product's pieces for this CTA (entries [e0, e1) of its issue
+// stream). i counts the pieces this CTA issued during the launch (ring slot i % kStages) and
+// cur is the slot of the latest one. The multi-RHS kernels (R > 1) skip the aux copies.
+// Returns false when a wait for a free slot gave up (status bit 2 set).
+template <int FMT, int PH, int R>
+__device__ bool produce(const DevLayout &L, uint32_t e0, uint32_t e1, uint8_t *smem, uint64_t *full,
+                        uint64_t *empty, uint32_t &i, uint32_t &cur) {
   constexpr uint32_t esz = Tr<FMT>::esz;
-  constexpr size_t slot = slot_bytes<FMT, PH>();
+  constexpr size_t slot = slot_bytes<FMT, PH, R>();
   const int lane = threadIdx.x & 31;
   const uint8_t *xsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.xperm32)
                                          : reinterpret_cast<const uint8_t *>(L.xperm64);
@@ -234,13 +285,10 @@ __device__ void producer(const DevLayout &L, const PhaseDev &P, uint32_t e0, uin
                                          : reinterpret_cast<const uint8_t *>(L.tw64);
   const uint8_t *fsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.fac32)
                                          : reinterpret_cast<const uint8_t *>(L.fac64);
-  const uint4 *ent = reinterpret_cast<const uint4 *>(P.ent);
-  uint32_t i = 0;  // pieces issued
-  uint32_t cur = 0;
-  bool ok = true;
+  const uint4 *ent = reinterpret_cast<const uint4 *>(L.ph[PH].ent);
   // the stream is read 32 entries per coalesced load, one load ahead
   uint4 nxt = e0 + lane < e1 ? __ldg(ent + e0 + lane) : make_uint4(0, 0, 0, 0);
-  for (uint32_t e = e0; e < e1 && ok; e += 32) {
+  for (uint32_t e = e0; e < e1; e += 32) {
     const uint4 mine = nxt;
     if (e + 32 + lane < e1) nxt = __ldg(ent + e + 32 + lane);
     const uint32_t cnt = min(32u, e1 - e);
@@ -256,27 +304,40 @@ __device__ void producer(const DevLayout &L, const PhaseDev &P, uint32_t e0, uin
             good = 0;
           } else {
             const uint64_t off = (uint64_t(b & ~kIssuePiece) << 32) | a;
-            mbar_expect_tx(&full[s], c + d * esz);
+            mbar_expect_tx(&full[s], R == 1 ? c + d * esz : c);
             tma_load(smem + size_t(s) * slot, L.base + off, c, &full[s]);
           }
         }
-        ok = __shfl_sync(kFull, good, 0) != 0;
-        if (!ok) break;
+        if (!__shfl_sync(kFull, good, 0)) return false;
         cur = s;
         ++i;
-      } else if (lane == 0) {
+      } else if (R == 1 && lane == 0) {
         const uint32_t nelem = b & 0xffffu, which = b >> 16;
         const uint8_t *src = (which == 0 ? xsrc : which == 1 ? tsrc : fsrc) + size_t(a) * esz;
         tma_load(smem + size_t(cur) * slot + kPieceMax + 16 + size_t(c) * esz, src, nelem * esz, &full[cur]);
       }
     }
   }
+  return true;
+}
+
+template <int FMT, int PH, int R, int NB>
+__device__ void producer(const Jobs<NB> &J, uint8_t *smem, uint64_t *full, uint64_t *empty) {
+  const int lane = threadIdx.x & 31;
+  uint32_t i = 0, cur = 0;
+  int m = 0;
+  for (; m < J.n; ++m) {
+    const PhaseDev &P = J.j[m].L.ph[PH];
+    const uint32_t e0 = __ldg(P.cta_e0 + blockIdx.x), e1 = __ldg(P.cta_e0 + blockIdx.x + 1);
+    if (!produce<FMT, PH, R>(J.j[m].L, e0, e1, smem, full, empty, i, cur)) break;
+  }
   // the last copy issued into every slot has landed before the CTA exits
   if (lane == 0) {
+    uint32_t *status = J.j[m < J.n ? m : J.n - 1].L.status;
     const uint32_t first = i > uint32_t(kStages) ? i - kStages : 0;
     for (uint32_t j = first; j < i; ++j)
       if (!mbar_wait(&full[j % kStages], (j / kStages) & 1)) {
-        atomicOr(L.status, 4u);
+        atomicOr(status, 4u);
         break;
       }
   }
@@ -299,15 +360,16 @@ __device__ __forceinline__ int find_seg(const Seg *segs, int nseg, int c) {
 // Phase 1 consumers: one lane per X column slice, t_i m_min(W_i) (or a partial sum)
 // ---------------------------------------------------------------------------------------------
 template <int FMT>
-__device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty) {
+__device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                               uint64_t *empty) {
   using A = typename Tr<FMT>::A;
   constexpr size_t slot = slot_bytes<FMT, 0>();
   const int t = threadIdx.x, lane = t & 31;
-  for (uint32_t i = 0; i < np; ++i) {
-    const uint32_t s = i % kStages;
-    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
       atomicOr(L.status, 1u);
-      return;
+      return false;
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
@@ -380,20 +442,31 @@ __device__ void consume_phase1(const DevLayout &L, uint32_t np, uint8_t *smem, u
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
+  return true;
 }
 
 // Columns of blocks whose phase-1 work is split into chunks: sum the partial sums in chunk
-// order and apply the column factor (deterministic, no atomics).
-template <int FMT>
-__global__ void k_combine(DevLayout L) {
-  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < L.ncnt; i += int64_t(gridDim.x) * blockDim.x) {
-    const Combine c = L.comb[i];
+// order and apply the column factor (deterministic, no atomics). One product per blockIdx.y;
+// R = kRB handles the kRB right-hand sides of a multi-RHS pass.
+template <int FMT, int R, int NB>
+__global__ void k_combine(const __grid_constant__ Jobs<NB> J) {
+  const Job &jb = J.j[blockIdx.y];
+  const DevLayout &L = jb.L;
+  const int64_t total = int64_t(L.ncnt) * R;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+    const Combine c = L.comb[i / R];
+    const int q = int(i % R);
     double sum = 0.0;
-    for (uint32_t k = 0; k < c.nchunks; ++k) sum += L.partial[size_t(c.pbase) + k];
-    if constexpr (FMT == FMT_AFL32)
-      L.tw32[c.tidx] = float(sum * double(L.fac32[c.tidx]));
-    else
-      L.tw64[c.tidx] = sum * L.fac64[c.tidx];
+    if constexpr (R == 1) {
+      for (uint32_t k = 0; k < c.nchunks; ++k) sum += L.partial[size_t(c.pbase) + k];
+      if constexpr (FMT == FMT_AFL32)
+        L.tw32[c.tidx] = float(sum * double(L.fac32[c.tidx]));
+      else
+        L.tw64[c.tidx] = sum * L.fac64[c.tidx];
+    } else {
+      for (uint32_t k = 0; k < c.nchunks; ++k) sum += jb.part[(size_t(c.pbase) + k) * kRB + q];
+      jb.tw[size_t(c.tidx) * kRB + q] = float(sum * double(L.fac32[c.tidx]));
+    }
   }
 }
 
@@ -423,21 +496,21 @@ __device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const 
 // write their products to a padded shared-memory tile and sum it transposed (a lane per row)
 // ---------------------------------------------------------------------------------------------
 template <int FMT>
-__device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full, uint64_t *empty,
-                               double *red, float *tiles, double *__restrict__ y) {
+__device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                               uint64_t *empty, double *red, float *tiles, double *__restrict__ y,
+                               uint32_t &parity) {
   using A = typename Tr<FMT>::A;
   constexpr size_t slot = slot_bytes<FMT, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   Comp32 acc[4];  // rows lane + 16 k (lanes 0..15) of the leaf: this warp's columns so far
-  uint32_t parity = 0;
   int64_t gi = 0;
   double yold = 0.0;  // y of this thread's row, read when the leaf starts
   float *tile = tiles + warp * (16 * 33);
-  for (uint32_t i = 0; i < np; ++i) {
-    const uint32_t s = i % kStages;
-    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
       atomicOr(L.status, 1u);
-      return;
+      return false;
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
@@ -513,6 +586,7 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
+  return true;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -520,19 +594,18 @@ __device__ void consume_phase2(const DevLayout &L, uint32_t np, uint8_t *smem, u
 // take the piece's column slices in turn; one FP64 fused multiply-add per value
 // ---------------------------------------------------------------------------------------------
 template <int FMT>
-__device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *smem, uint64_t *full,
-                                    uint64_t *empty, double *red, double *__restrict__ y) {
+__device__ bool consume_phase2_rows(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                    uint64_t *empty, double *red, double *__restrict__ y, uint32_t &parity) {
   constexpr size_t slot = slot_bytes<FMT, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   double a0 = 0.0, a1 = 0.0;
-  uint32_t parity = 0;
   int64_t gi = 0;
   double yold = 0.0;  // y of this thread's row, read when the leaf starts
-  for (uint32_t i = 0; i < np; ++i) {
-    const uint32_t s = i % kStages;
-    if (!mbar_wait(&full[s], (i / kStages) & 1)) {
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
       atomicOr(L.status, 1u);
-      return;
+      return false;
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
@@ -581,19 +654,246 @@ __device__ void consume_phase2_rows(const DevLayout &L, uint32_t np, uint8_t *sm
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
+  return true;
 }
 
-template <int FMT, int PH>
-__global__ void __launch_bounds__(kThreads) k_product(DevLayout L, double *__restrict__ y) {
+// ---------------------------------------------------------------------------------------------
+// Multi-RHS pass, phase 1 (FP32): as consume_phase1, but every lane keeps kRB dot products; the
+// x rows come from the pass's X_perm in global memory (kRB floats per row, through L1) and the
+// column factors from fac32.
+// ---------------------------------------------------------------------------------------------
+__device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                     uint64_t *empty) {
+  const DevLayout &L = jb.L;
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 0, kRB>();
+  const int t = threadIdx.x, lane = t & 31;
+  const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    float acc[kRB];
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) acc[q] = 0.f;
+    uint32_t G = 1;
+    const Seg *sgp = nullptr;
+    int j = 0;
+    bool lead = false;
+    if (t < int(ph->ncols)) {
+      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
+      const int rel = t - int(sg.cstart);
+      const int jj = rel >> sg.lg;
+      if (jj < int(sg.nc)) {
+        sgp = &sg;
+        j = jj;
+        G = 1u << sg.lg;
+        const int sub = rel & int(G - 1);
+        lead = sub == 0;
+        const uint32_t ch = Wd[sg.col_w + j];
+        const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
+        const int r0 = sub * kSubRows;
+        const int rc = min(kSubRows, int(sg.nr) - r0);
+        const float4 *xr = xp4 + (size_t(sg.gx) + r0) * (kRB / 4);
+        const ColDec c = col_dec((ch >> 16) & 0xffu, ch >> 24);
+#pragma unroll 4
+        for (int r = 0; r < rc; ++r) {
+          float v;
+          if (c.fast32)
+            v = dec_f32(code32_at(Dc, uint32_t(r0 + r) * c.w), c);
+          else if (c.narrow)
+            v = float(dec_f64(code32_at(Dc, uint32_t(r0 + r) * c.w), c));
+          else
+            v = float(dec_f64(code64_at(Dc, uint32_t(r0 + r) * c.w), c));
+#pragma unroll
+          for (int h = 0; h < kRB / 4; ++h) {
+            const float4 xv = __ldg(xr + r * (kRB / 4) + h);
+            acc[4 * h] = fmaf(v, xv.x, acc[4 * h]);
+            acc[4 * h + 1] = fmaf(v, xv.y, acc[4 * h + 1]);
+            acc[4 * h + 2] = fmaf(v, xv.z, acc[4 * h + 2]);
+            acc[4 * h + 3] = fmaf(v, xv.w, acc[4 * h + 3]);
+          }
+        }
+      }
+    }
+    // the G lanes of a column (an aligned group) sum their row parts in a fixed order
+#pragma unroll
+    for (uint32_t o = 1; o < 4; o <<= 1) {
+#pragma unroll
+      for (int q = 0; q < kRB; ++q) {
+        const float v = __shfl_xor_sync(kFull, acc[q], o);
+        if (o < G) acc[q] += v;
+      }
+    }
+    if (lead) {
+      const Seg &sg = *sgp;
+      if (sg.x.nchunks == 1) {
+        const float f = __ldg(L.fac32 + sg.tidx + j);
+        float4 *dst = reinterpret_cast<float4 *>(jb.tw + (size_t(sg.tidx) + j) * kRB);
+#pragma unroll
+        for (int h = 0; h < kRB / 4; ++h)
+          dst[h] = make_float4(acc[4 * h] * f, acc[4 * h + 1] * f, acc[4 * h + 2] * f, acc[4 * h + 3] * f);
+      } else {
+        double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * kRB;
+#pragma unroll
+        for (int q = 0; q < kRB; ++q) dst[q] = double(acc[q]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Multi-RHS pass, phase 2 (FP32): lanes are the rows of the leaf (lane, lane + 32), the warps
+// take the piece's column slices in turn; a value is decoded once and multiplied by the kRB
+// multipliers of its column (t m_min(W) of the pass, or X row times m_min for dense blocks).
+// FP32 sums over the <= 32 columns a warp takes from one piece, compensated FP32 pairs across
+// pieces, FP64 for the sum over warps and into Y.
+// ---------------------------------------------------------------------------------------------
+__device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                     uint64_t *empty, double *red, float *mbufs) {
+  const DevLayout &L = jb.L;
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 1, kRB>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
+  const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
+  Comp32 c0[kRB], c1[kRB];
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+#pragma unroll
+      for (int q = 0; q < kRB; ++q) {
+        c0[q].reset();
+        c1[q].reset();
+      }
+    }
+    float a0[kRB], a1[kRB];
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) a0[q] = a1[q] = 0.f;
+    const bool ok0 = lane < nr, ok1 = lane + 32 < nr;
+    const int ncols = ph->ncols, nseg = ph->nseg;
+    // the multipliers of this warp's (<= 32) columns, loaded by one lane each (all loads in
+    // flight together) into the warp's buffer: one global-memory latency per piece
+    float4 *mb = reinterpret_cast<float4 *>(mbufs) + warp * 32 * (kRB / 4);
+    {
+      const int col = warp + kCWarps * lane;
+      if (col < ncols) {
+        const Seg &sg = segs[find_seg(segs, nseg, col)];
+        const int j = col - int(sg.cstart);
+        float4 lo, hi;
+        if (sg.kind == SEG_DENSE) {
+          const float mm = float(sg.m_min);
+          const float4 x0 = __ldg(xp4 + (size_t(sg.gx) + j) * (kRB / 4));
+          const float4 x1 = __ldg(xp4 + (size_t(sg.gx) + j) * (kRB / 4) + 1);
+          lo = make_float4(x0.x * mm, x0.y * mm, x0.z * mm, x0.w * mm);
+          hi = make_float4(x1.x * mm, x1.y * mm, x1.z * mm, x1.w * mm);
+        } else {
+          lo = __ldg(tw4 + (size_t(sg.gx) + j) * (kRB / 4));
+          hi = __ldg(tw4 + (size_t(sg.gx) + j) * (kRB / 4) + 1);
+        }
+        mb[lane * 2] = lo;
+        mb[lane * 2 + 1] = hi;
+      }
+    }
+    __syncwarp();
+    int si = 0;
+    for (int col = warp, k = 0; col < ncols; col += kCWarps, ++k) {
+      while (si + 1 < nseg && int(segs[si + 1].cstart) <= col) ++si;
+      const Seg &sg = segs[si];
+      const int j = col - int(sg.cstart);
+      uint32_t start, e, m;
+      if (sg.kind == SEG_DENSE) {
+        e = sg.col_w & 0xffu;
+        m = (sg.col_w >> 8) & 0xffu;
+        start = uint32_t(sg.data_w) * 32u + uint32_t(j * nr) * (1u + e + m);
+      } else {
+        const uint32_t ch = Wd[sg.col_w + j];
+        e = (ch >> 16) & 0xffu;
+        m = ch >> 24;
+        start = (uint32_t(sg.data_w) + (ch & 0xffffu)) * 32u;
+      }
+      const float4 mlo = mb[k * 2], mhi = mb[k * 2 + 1];
+      const ColDec c = col_dec(e, m);
+      float v0 = 0.f, v1 = 0.f;
+      if (c.fast32) {
+        if (ok0) v0 = dec_f32(code32_at(Wd, start + uint32_t(lane) * c.w), c);
+        if (ok1) v1 = dec_f32(code32_at(Wd, start + uint32_t(lane + 32) * c.w), c);
+      } else if (c.narrow) {
+        if (ok0) v0 = float(dec_f64(code32_at(Wd, start + uint32_t(lane) * c.w), c));
+        if (ok1) v1 = float(dec_f64(code32_at(Wd, start + uint32_t(lane + 32) * c.w), c));
+      } else {
+        if (ok0) v0 = float(dec_f64(code64_at(Wd, start + uint32_t(lane) * c.w), c));
+        if (ok1) v1 = float(dec_f64(code64_at(Wd, start + uint32_t(lane + 32) * c.w), c));
+      }
+      const float mv[kRB] = {mlo.x, mlo.y, mlo.z, mlo.w, mhi.x, mhi.y, mhi.z, mhi.w};
+#pragma unroll
+      for (int q = 0; q < kRB; ++q) {
+        a0[q] = fmaf(v0, mv[q], a0[q]);
+        a1[q] = fmaf(v1, mv[q], a1[q]);
+      }
+    }
+    __syncwarp();  // the multiplier buffer is refilled for the next piece
+#pragma unroll
+    for (int q = 0; q < kRB; ++q) {
+      c0[q].add(a0[q]);
+      c1[q].add(a1[q]);
+    }
+    if (flags & PF_END_LEAF) {
+      // per-warp row sums of the kRB right-hand sides, then per (row, rhs) the sum over the
+      // warps in fixed order; the buffer is reused only after a second barrier
+#pragma unroll
+      for (int q = 0; q < kRB; ++q) {
+        red[(warp * 64 + lane) * kRB + q] = c0[q].value();
+        red[(warp * 64 + lane + 32) * kRB + q] = c1[q].value();
+      }
+      bar_consumers();
+      const uint32_t row0 = ph->row0;
+      for (int idx = t; idx < nr * jb.nrhs; idx += kConsumers) {
+        const int row = idx / jb.nrhs, q = idx - row * jb.nrhs;
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCWarps; ++w) sum += red[(w * 64 + row) * kRB + q];
+        double *yp = jb.y + size_t(q) * size_t(jb.ldy) + __ldg(L.perm + row0 + uint32_t(row));
+        *yp += sum;  // the only update of this entry (its leaf has one owner CTA)
+      }
+      bar_consumers();
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// Persistent product kernel over the products of one launch (J.n <= NB). Every CTA walks its
+// range of each product's piece stream in turn; the ring slots and their mbarrier phases run on
+// across products.
+template <int FMT, int PH, int R, int NB>
+__global__ void __launch_bounds__(kThreads) k_product(const __grid_constant__ Jobs<NB> J) {
   extern __shared__ __align__(128) uint8_t smem[];
-  constexpr size_t slot = slot_bytes<FMT, PH>();
+  constexpr size_t slot = slot_bytes<FMT, PH, R>();
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
   uint64_t *empty = full + kStages;
   double *red = reinterpret_cast<double *>(empty + kStages);
   float *tiles = reinterpret_cast<float *>(red + 2 * kCWarps * 64);
-  const PhaseDev &P = L.ph[PH];
-  const uint32_t e0 = P.cta_e0[blockIdx.x], e1 = P.cta_e0[blockIdx.x + 1];
-  const uint32_t np = P.cta_np[blockIdx.x];
+  uint32_t np_all = 0;
+  for (int m = 0; m < J.n; ++m) np_all += __ldg(J.j[m].L.ph[PH].cta_np + blockIdx.x);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -602,17 +902,31 @@ __global__ void __launch_bounds__(kThreads) k_product(DevLayout L, double *__res
     fence_mbar_init();
   }
   __syncthreads();
-  if (np == 0) return;
+  if (np_all == 0) return;
   if (threadIdx.x >= kConsumers) {
-    producer<FMT, PH>(L, P, e0, e1, smem, full, empty);
+    producer<FMT, PH, R, NB>(J, smem, full, empty);
     return;
   }
-  if constexpr (PH == 0)
-    consume_phase1<FMT>(L, np, smem, full, empty);
-  else if constexpr (FMT == FMT_AFL32)
-    consume_phase2<FMT>(L, np, smem, full, empty, red, tiles, y);
-  else
-    consume_phase2_rows<FMT>(L, np, smem, full, empty, red, y);
+  uint32_t it = 0, parity = 0;
+  for (int m = 0; m < J.n; ++m) {
+    const Job &jb = J.j[m];
+    const uint32_t np = __ldg(jb.L.ph[PH].cta_np + blockIdx.x);
+    bool ok;
+    if constexpr (R > 1) {
+      if constexpr (PH == 0)
+        ok = consume_phase1_multi(jb, np, it, smem, full, empty);
+      else
+        ok = consume_phase2_multi(jb, np, it, smem, full, empty, red,
+                                  reinterpret_cast<float *>(red + kCWarps * 64 * kRB));
+    } else if constexpr (PH == 0) {
+      ok = consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
+    } else if constexpr (FMT == FMT_AFL32) {
+      ok = consume_phase2<FMT>(jb.L, np, it, smem, full, empty, red, tiles, jb.y, parity);
+    } else {
+      ok = consume_phase2_rows<FMT>(jb.L, np, it, smem, full, empty, red, jb.y, parity);
+    }
+    if (!ok) return;
+  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -681,9 +995,21 @@ struct DevProps {
 std::mutex g_props_mu;
 DevProps g_props[64];
 
-template <int FMT, int PH>
+template <int FMT, int PH, int R, int NB>
 void set_smem_attr() {
-  cudaFuncSetAttribute(k_product<FMT, PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem_bytes<FMT, PH>()));
+  cudaFuncSetAttribute(k_product<FMT, PH, R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       int(smem_bytes<FMT, PH, R>()));
+}
+template <int NB>
+void set_smem_attrs() {
+  set_smem_attr<FMT_AFL32, 0, 1, NB>();
+  set_smem_attr<FMT_AFL32, 1, 1, NB>();
+  set_smem_attr<FMT_AFL64, 0, 1, NB>();
+  set_smem_attr<FMT_AFL64, 1, 1, NB>();
+  set_smem_attr<FMT_RAW64, 0, 1, NB>();
+  set_smem_attr<FMT_RAW64, 1, 1, NB>();
+  set_smem_attr<FMT_AFL32, 0, kRB, NB>();
+  set_smem_attr<FMT_AFL32, 1, kRB, NB>();
 }
 
 const DevProps &props(int dev) {
@@ -694,15 +1020,13 @@ const DevProps &props(int dev) {
     cudaGetDevice(&cur);
     if (cur != dev) cudaSetDevice(dev);
     cudaDeviceGetAttribute(&P.sms, cudaDevAttrMultiProcessorCount, dev);
-    set_smem_attr<FMT_AFL32, 0>();
-    set_smem_attr<FMT_AFL32, 1>();
-    set_smem_attr<FMT_AFL64, 0>();
-    set_smem_attr<FMT_AFL64, 1>();
-    set_smem_attr<FMT_RAW64, 0>();
-    set_smem_attr<FMT_RAW64, 1>();
+    set_smem_attrs<1>();
+    set_smem_attrs<kMaxBatch>();
     int o0 = 0, o1 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL32, 0>, kThreads, smem_bytes<FMT_AFL32, 0>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL32, 1>, kThreads, smem_bytes<FMT_AFL32, 1>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL32, 0, 1, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 0>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL32, 1, 1, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 1>());
     P.occ[0] = o0 < 1 ? 1 : o0;
     P.occ[1] = o1 < 1 ? 1 : o1;
     if (cur != dev) cudaSetDevice(cur);
@@ -716,14 +1040,35 @@ int cuda_status(const char *what) {
   return HLR_OK;
 }
 
-template <int FMT>
-void launch_phases(const Handle &H, double *y, cudaStream_t st, cudaEvent_t *ev) {
-  const DevLayout &L = H.L;
+// Launch the four kernels of the products in J (all of one device, so all share the persistent
+// grid sizes): permute, phase 1, combine of split blocks, phase 2. ev (optional): 4 events.
+template <int FMT, int R, int NB>
+void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev) {
+  if (J.n <= 0) return;
+  int64_t nmax = 0, ncnt = 0;
+  uint32_t np0 = 0, np1 = 0;
+  for (int m = 0; m < J.n; ++m) {
+    const DevLayout &L = J.j[m].L;
+    nmax = std::max<int64_t>(nmax, L.n);
+    ncnt = std::max<int64_t>(ncnt, L.ncnt);
+    np0 += uint32_t(L.ph[0].np);
+    np1 += uint32_t(L.ph[1].np);
+  }
+  const int nct0 = J.j[0].L.ph[0].nct, nct1 = J.j[0].L.ph[1].nct;
+  const dim3 gp(unsigned(std::min<int64_t>((nmax + 255) / 256, 4096)), unsigned(J.n));
+  if (ev) cudaEventRecord(ev[0], st);
+  if constexpr (R == 1)
+    k_permute<NB><<<gp, 256, 0, st>>>(J);
+  else
+    k_permute_multi<NB><<<gp, 256, 0, st>>>(J);
   if (ev) cudaEventRecord(ev[1], st);
-  if (L.ph[0].np > 0) k_product<FMT, 0><<<L.ph[0].nct, kThreads, smem_bytes<FMT, 0>(), st>>>(L, y);
-  if (L.ncnt > 0) k_combine<FMT><<<int(std::min<int64_t>((L.ncnt + 255) / 256, 1024)), 256, 0, st>>>(L);
+  if (np0 > 0) k_product<FMT, 0, R, NB><<<nct0, kThreads, smem_bytes<FMT, 0, R>(), st>>>(J);
+  if (ncnt > 0) {
+    const dim3 gc(unsigned(std::min<int64_t>((ncnt * R + 255) / 256, 1024)), unsigned(J.n));
+    k_combine<FMT, R, NB><<<gc, 256, 0, st>>>(J);
+  }
   if (ev) cudaEventRecord(ev[2], st);
-  if (L.ph[1].np > 0) k_product<FMT, 1><<<L.ph[1].nct, kThreads, smem_bytes<FMT, 1>(), st>>>(L, y);
+  if (np1 > 0) k_product<FMT, 1, R, NB><<<nct1, kThreads, smem_bytes<FMT, 1, R>(), st>>>(J);
   if (ev) cudaEventRecord(ev[3], st);
 }
 
@@ -742,6 +1087,15 @@ cudaEvent_t *profile_slot(Handle &H, int flags) {
   return reinterpret_cast<cudaEvent_t *>(&H.prof_ev[4 * size_t(H.prof_n++)]);
 }
 
+Job single_job(const Handle &H, const double *x, double *y) {
+  Job j{};
+  j.L = H.L;
+  j.x = x;
+  j.y = y;
+  j.nrhs = 1;
+  return j;
+}
+
 }  // namespace
 
 int ctas_per_phase(int device, int nct[2]) {
@@ -754,21 +1108,140 @@ int ctas_per_phase(int device, int nct[2]) {
 
 int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const DevLayout &L = H.L;
   cudaGetLastError();
   props(H.device);
   cudaEvent_t *ev = profile_slot(H, flags);
   const int acc = flags & 0xff;
-  const int gp = int(std::min<int64_t>((L.n + 255) / 256, 4096));
-  if (ev) cudaEventRecord(ev[0], st);
-  k_permute<<<gp, 256, 0, st>>>(L.perm, L.n, x, L.xperm64, L.xperm32);
-  if (L.raw)
-    launch_phases<FMT_RAW64>(H, y, st, ev);
+  Jobs<1> J{};
+  J.n = 1;
+  J.j[0] = single_job(H, x, y);
+  if (H.L.raw)
+    launch_jobs<FMT_RAW64, 1, 1>(J, st, ev);
   else if (acc == HLR_ACC_FP32)
-    launch_phases<FMT_AFL32>(H, y, st, ev);
+    launch_jobs<FMT_AFL32, 1, 1>(J, st, ev);
   else
-    launch_phases<FMT_AFL64>(H, y, st, ev);
+    launch_jobs<FMT_AFL64, 1, 1>(J, st, ev);
   return cuda_status("hlr_matvec: launch");
+}
+
+// Scratch of multi-RHS passes: `passes` sets of (X_perm, t m_min(W), partial sums) per handle,
+// allocated on first use and grown when a request needs more passes.
+static int multi_scratch(Handle &H, int passes, float **xp, float **tw, double **part, size_t *stride) {
+  const size_t n = size_t(H.L.n), rs = size_t(H.info.rank_sum);
+  const size_t b_xp = (((n + 8) * kRB * 4) + 255) & ~size_t(255);
+  const size_t b_tw = (((rs + 8) * kRB * 4) + 255) & ~size_t(255);
+  const size_t b_pt = (((size_t(H.part_total) + 1) * kRB * 8) + 255) & ~size_t(255);
+  const size_t per = b_xp + b_tw + b_pt;
+  if (H.multi_passes < passes) {
+    if (H.multi_ws) {
+      cudaFree(H.multi_ws);
+      H.multi_ws = nullptr;
+      H.multi_passes = 0;
+    }
+    if (cudaMalloc(&H.multi_ws, per * size_t(passes)) != cudaSuccess) {
+      cudaGetLastError();
+      H.multi_ws = nullptr;
+      return set_error(HLR_ERR_OOM, "hlr_matvec_batched: multi-RHS scratch allocation failed");
+    }
+    H.multi_passes = passes;
+  }
+  uint8_t *b = static_cast<uint8_t *>(H.multi_ws);
+  *xp = reinterpret_cast<float *>(b);
+  *tw = reinterpret_cast<float *>(b + b_xp);
+  *part = reinterpret_cast<double *>(b + b_xp + b_tw);
+  *stride = per;
+  return HLR_OK;
+}
+
+namespace {
+// Accumulates the products of one kernel class and launches them in groups of <= kMaxBatch.
+// Two products of one group must not share scratch: the same handle appears at most once among
+// the single-RHS products of a group and each (handle, pass) at most once among the passes.
+template <int FMT, int R>
+struct Batcher {
+  Jobs<kMaxBatch> J{};
+  std::vector<std::pair<const Handle *, int>> keys;
+  cudaStream_t st;
+  int device = -1;
+  explicit Batcher(cudaStream_t s) : st(s) { J.n = 0; }
+  void flush() {
+    if (J.n > 0) launch_jobs<FMT, R, kMaxBatch>(J, st, nullptr);
+    J.n = 0;
+    keys.clear();
+  }
+  void add(const Handle *H, int pass, const Job &jb) {
+    const auto key = std::make_pair(H, pass);
+    bool clash = J.n >= kMaxBatch;
+    for (const auto &k : keys) clash = clash || k == key;
+    if (clash) flush();
+    J.j[J.n++] = jb;
+    keys.push_back(key);
+  }
+};
+}  // namespace
+
+int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *const *X, const int64_t *ldx,
+                 double *const *Y, const int64_t *ldy, int flags, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  if (nreq <= 0) return HLR_OK;
+  const int dev = H[0]->device;
+  for (int q = 0; q < nreq; ++q)
+    if (H[q]->device != dev) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: handles of different devices");
+  props(dev);
+  const bool fp32 = (flags & 0xff) == HLR_ACC_FP32;
+  Batcher<FMT_AFL32, 1> b32(st);
+  Batcher<FMT_AFL64, 1> b64(st);
+  Batcher<FMT_RAW64, 1> braw(st);
+  Batcher<FMT_AFL32, kRB> bm(st);
+  // pass scratch first (growing it frees the old one, which no pending product may still use)
+  for (int q = 0; q < nreq; ++q) {
+    if (nrhs[q] <= 1 || !fp32 || H[q]->L.raw) continue;
+    int passes = 0;
+    for (int k = 0; k < nreq; ++k)
+      if (H[k] == H[q] && nrhs[k] > 1) passes = std::max(passes, (nrhs[k] + kRB - 1) / kRB);
+    float *xp, *tw;
+    double *part;
+    size_t stride;
+    if (int rc = multi_scratch(*H[q], passes, &xp, &tw, &part, &stride)) return rc;
+  }
+  for (int q = 0; q < nreq; ++q) {
+    Handle &Hq = *H[q];
+    const int r = nrhs[q];
+    if (r <= 0) continue;
+    if (r > 1 && fp32 && !Hq.L.raw) {
+      const int passes = (r + kRB - 1) / kRB;
+      float *xp, *tw;
+      double *part;
+      size_t stride;
+      if (int rc = multi_scratch(Hq, passes, &xp, &tw, &part, &stride)) return rc;
+      for (int p = 0; p < passes; ++p) {
+        Job jb = single_job(Hq, X[q] + size_t(p) * kRB * size_t(ldx[q]), Y[q] + size_t(p) * kRB * size_t(ldy[q]));
+        jb.ldx = ldx[q];
+        jb.ldy = ldy[q];
+        jb.nrhs = std::min(kRB, r - p * kRB);
+        jb.xp = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(xp) + p * stride);
+        jb.tw = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tw) + p * stride);
+        jb.part = reinterpret_cast<double *>(reinterpret_cast<uint8_t *>(part) + p * stride);
+        bm.add(&Hq, p, jb);
+      }
+    } else {
+      for (int c = 0; c < r; ++c) {
+        const Job jb = single_job(Hq, X[q] + size_t(c) * size_t(ldx[q]), Y[q] + size_t(c) * size_t(ldy[q]));
+        if (Hq.L.raw)
+          braw.add(&Hq, -1, jb);
+        else if (fp32)
+          b32.add(&Hq, -1, jb);
+        else
+          b64.add(&Hq, -1, jb);
+      }
+    }
+  }
+  b32.flush();
+  b64.flush();
+  braw.flush();
+  bm.flush();
+  return cuda_status("hlr_matvec_batched: launch");
 }
 
 int profile_read(Handle &H, double *ms, int *calls) {

@@ -110,6 +110,7 @@ class Builder {
       s.cstart = uint16_t(ncols_);
       s.nr = uint16_t(nr);
       s.xs = add_aux(0, B.col0 + j0, fit);
+      s.gx = uint32_t(B.col0 + j0);
       s.data_w = uint16_t(data_.size());
       s.col_w = uint16_t((in_.raw ? 0 : in_.prm[u].e) | ((in_.raw ? 0 : in_.prm[u].m) << 8));
       s.m_min = in_.raw ? 1.0 : in_.prm[u].m_min;
@@ -178,12 +179,13 @@ class Builder {
         s.xs = add_aux(0, xoff, nr);
         s.fs = add_aux(2, L.tbase + i0, fit);
         s.tidx = L.tbase + uint32_t(i0);
-        s.cnt = L.cbase + uint32_t(i0);
+        s.gx = uint32_t(xoff);
         s.x.pbase = L.part0 + uint32_t(i0) * L.nchunks;
         s.x.chunk = chunk;
         s.x.nchunks = L.nchunks;
       } else {
         s.xs = add_aux(1, L.tbase + i0, fit);
+        s.gx = L.tbase + uint32_t(i0);
       }
       uint32_t woff = 0;
       for (int i = i0; i < i0 + fit; ++i) {

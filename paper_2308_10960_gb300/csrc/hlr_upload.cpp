@@ -375,6 +375,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   L.raw = afl ? 0 : 1;
   H->nunits = nunits;
   H->values = values;
+  H->part_total = po.part_total;
   if (want_map) {
     H->slice_src = std::move(po.slice_src);
     H->slice_dst = std::move(po.slice_dst);
@@ -451,6 +452,7 @@ extern "C" int hlr_free(hlr_handle h) {
   cudaError_t ce = cudaDeviceSynchronize();
   if (H->arena) cudaFree(H->arena);
   if (H->cg_ws) cudaFree(H->cg_ws);
+  if (H->multi_ws) cudaFree(H->multi_ws);
   for (void *e : H->prof_ev)
     if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
   if (ce != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string("hlr_free: ") + cudaGetErrorString(ce));
