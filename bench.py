@@ -43,9 +43,16 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS comparison legs")
-    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48"],
+    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve"],
                     help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
-                         "uneven size with 1/8/32 right-hand sides in one batched launch sequence")
+                         "uneven size with 1/8/32 right-hand sides in one batched launch sequence; serve: "
+                         "Poisson requests (70%% products, 30%% CG solves) against resident Matern matrices")
+    ap.add_argument("--serve-mats", type=int, default=16)
+    ap.add_argument("--serve-min-n", type=int, default=16384)
+    ap.add_argument("--serve-max-n", type=int, default=262144)
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
+    ap.add_argument("--serve-rates", default="20,100,500", help="arrival rates (requests/s) to sweep")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     return ap.parse_args()
 
 
@@ -504,6 +511,74 @@ def run_batch(args, world: int, rank: int, local: int):
         A.free()
 
 
+def run_serve(args, world: int, rank: int, local: int):
+    """Serving: --serve-mats Matern matrices (n log-spaced in [--serve-min-n, --serve-max-n],
+    points seed 200 + i) resident under an HBM budget; for every arrival rate a Poisson stream
+    (seed 5) of --serve-requests requests, 70 % products and 30 % CG solves to 1e-8, over the
+    matrices uniformly (seed 6). value = products' and solves' algorithmic bytes / makespan at the
+    highest rate; p50/p99 latency per rate and kind."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+    from paper_2308_10960_gb300 import serve
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    k = args.serve_mats
+    sizes = [int(round(math.exp(math.log(args.serve_min_n) + (math.log(args.serve_max_n) - math.log(args.serve_min_n))
+                                * i / max(1, k - 1)))) for i in range(k)]
+    t0 = time.perf_counter()
+    host = {}
+    for i, n in enumerate(sizes):
+        p = synth.matern_problem(n, seed=200 + i)
+        host[f"m{i}"] = hg.build_kernel_hmatrix(p.points, "matern15", args.eps, scale=p.params["scale"],
+                                                diag=p.params["diag"])
+    be = serve.GpuBackend(host)
+    t_build = time.perf_counter() - t0
+    budget = int(args.serve_budget_gb * 1e9)
+    names = sorted(host, key=lambda m: int(m[1:]))
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    g = np.random.default_rng(6)
+    per_rate = {}
+    last = None
+    clocks = ClockSampler(local)
+    clocks.start()
+    for ri, rate in enumerate(rates):
+        arr = serve.poisson_arrivals(args.serve_requests, rate, 5 + ri)
+        reqs = []
+        for i in range(args.serve_requests):
+            m = names[int(g.integers(len(names)))]
+            kind = "solve" if g.random() < 0.3 else "matvec"
+            x = torch.from_numpy(synth.rhs(host[m].n, 7000 + 100 * ri + i)).to(dev)
+            reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000))
+        torch.cuda.synchronize()
+        srv = serve.Server(be, budget_bytes=budget, cg_workers=4, max_rhs=32)
+        srv.preload(names)           # the matrices are resident before the requests arrive
+        torch.cuda.synchronize()
+        st = srv.run(reqs)
+        d = st.as_dict()
+        d["cg_iterations_mean"] = float(np.mean([r.iters for r in reqs if r.kind == "solve"] or [0]))
+        d["cg_true_relres_max"] = float(max([r.relres for r in reqs if r.kind == "solve"] or [0]))
+        per_rate[str(rate)] = d
+        last = d
+    clk = clocks.stop()
+    if rank == 0:
+        peaks = measured_peaks()
+        solve_p99 = last["latency_ms"].get("solve", {}).get("p99")
+        out = {"metric": METRIC, "value": last["GB/s"] * world, "unit": UNIT, "n_gpus": world,
+               "steps": args.serve_requests, "warmup": 0, "ms_per_step": last["makespan_s"] * 1e3 / args.serve_requests,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"serving {k} Matern nu=1.5 matrices n {sizes[0]}..{sizes[-1]}, eps={args.eps:g}, "
+                                      f"Poisson arrivals, 70% products / 30% CG to 1e-8, budget {args.serve_budget_gb:g} GB",
+                          "sizes": sizes, "rates": rates, "requests_per_rate": args.serve_requests,
+                          "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+               "p99_solve_ms": solve_p99, "per_rate": per_rate, "pct_hbm_peak": last["GB/s"] / peaks["hbm_gbs"],
+               "build_s": t_build, "clocks": clk,
+               "resident_bytes": {m: be.device_bytes(m) for m in names}}
+        print(json.dumps(out), flush=True)
+    be.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -521,6 +596,8 @@ def main():
         return
     if args.workload == "batch48":
         run_batch(args, world, rank, local)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

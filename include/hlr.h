@@ -51,6 +51,10 @@ extern "C" {
 #define HLR_ACC_FP32 1  /* decode to FP32, FP32 sums inside a block, FP64 across blocks into y */
 #define HLR_PROFILE  0x100 /* OR-ed into flags: record CUDA events around each kernel launch of the
                               product on cuda_stream, for hlr_profile_read (adds no synchronisation) */
+#define HLR_MULTI    0x200 /* OR-ed into hlr_matvec_batched flags with HLR_ACC_FP32: run every
+                              request, single columns included, through the multi-right-hand-side
+                              kernels, whose result for a column does not depend on the other
+                              columns or requests it is launched with */
 
 typedef uint64_t hlr_handle; /* 0 is never a valid handle */
 
@@ -124,16 +128,31 @@ int hlr_matvec_host(hlr_handle h, const double *x_host, double *y_host, int flag
 /* Many products in one launch sequence: for request q, Y_q += A~_q X_q with X_q, Y_q holding
  * nrhs[q] columns (leading dimensions ldx[q], ldy[q] >= n_q, column-major). The pointer
  * arrays are host arrays of device pointers. Requests may repeat a handle only if their Y
- * blocks do not overlap. Errors: HLR_ERR_INVALID, HLR_ERR_OOM, HLR_ERR_CUDA. */
+ * blocks do not overlap. Products of the same kind go into persistent launches of up to 64
+ * products each (permute, phase 1, combine, phase 2 per launch group; the job list is a kernel
+ * parameter, so no device memory is allocated per call and the call can be captured in a CUDA
+ * graph once the scratch below exists). With HLR_ACC_FP32, requests with several columns
+ * (and every request under HLR_MULTI) run in passes of 8 columns that decode each value once;
+ * their pass scratch is allocated per handle on first use (call once before capturing).
+ * FP64 accumulation and plain FP64 storage run one product per column.
+ * Errors: HLR_ERR_INVALID, HLR_ERR_OOM, HLR_ERR_CUDA. Section 5.4 (applied per column). */
 int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
                        const double *const *X_dev, const int64_t *ldx,
                        double *const *Y_dev, const int64_t *ldy, int flags, void *cuda_stream);
 
 /* Unpreconditioned conjugate gradients for A~ x = b (A~ symmetric positive definite), with
- * x_dev as initial guess on entry and the solution on return. Stops when the recursive
- * residual satisfies ||r|| <= rtol ||b||. Inner products and vector updates are FP64;
- * the products use flags. Synchronous (returns *iters and *relres, the relative TRUE
- * residual ||b - A~ x|| / ||b|| of the returned x). HLR_ERR_NOCONV when maxit is reached. */
+ * x_dev as initial guess on entry and the solution on return. Inner products (reduced in a
+ * fixed order) and vector updates are FP64. flags:
+ *  HLR_ACC_FP64: CG with FP64-accumulation products, stopped when the recursive residual has
+ *                ||r|| <= rtol ||b||;
+ *  HLR_ACC_FP32: iterative refinement: the true residual b - A~ x is formed with the FP64
+ *                product, the correction A~ d = r is solved by CG with the FP32-accumulation
+ *                product to a relative 1e-3 (or what the last step needs), x += d, until the
+ *                TRUE residual has ||b - A~ x|| <= rtol ||b||.
+ * Synchronous (one small device-to-host read per iteration). Returns *iters (CG iterations,
+ * all corrections together) and *relres, the relative TRUE residual ||b - A~ x|| / ||b|| of
+ * the returned x (FP64 product). HLR_ERR_NOCONV when maxit is reached. Workspace of 5n doubles
+ * is allocated per handle on the first solve. */
 int hlr_solve_cg(hlr_handle h, const double *b_dev, double *x_dev, double rtol, int maxit,
                  int flags, void *cuda_stream, int *iters, double *relres);
 

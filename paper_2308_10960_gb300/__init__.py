@@ -185,9 +185,11 @@ def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None) -> DeviceHM
     return DeviceHMatrix(h.value)
 
 
-def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None):
+def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None, multi=False):
     """Y_q += A~_q X_q for every request q (X_q, Y_q: n_q x r_q column-major float64 CUDA tensors,
-    i.e. tensors of shape (r_q, n_q) in row-major memory, or 1-D of length n_q)."""
+    i.e. tensors of shape (r_q, n_q) in row-major memory, or 1-D of length n_q). multi=True
+    (FP32 only) runs single columns through the multi-RHS kernels too, so that a column's result
+    does not depend on what it is batched with."""
     q = len(mats)
     hs = (C.c_uint64 * q)(*[m.handle for m in mats])
     nr = (C.c_int32 * q)()
@@ -202,7 +204,8 @@ def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None):
         yp[i] = _dev_ptr(Y, m.n * r)
         lx[i] = m.n
         ly[i] = m.n
-    B.check(B.lib.hlr_matvec_batched(q, hs, nr, xp, lx, yp, ly, _ACC[acc], _stream_ptr(stream)))
+    flags = _ACC[acc] | (B.HLR_MULTI if multi else 0)
+    B.check(B.lib.hlr_matvec_batched(q, hs, nr, xp, lx, yp, ly, flags, _stream_ptr(stream)))
 
 
 class HostHMatrix:

@@ -29,6 +29,7 @@ HLR_FMT_FP64 = 2
 HLR_ACC_FP64 = 0
 HLR_ACC_FP32 = 1
 HLR_PROFILE = 0x100
+HLR_MULTI = 0x200
 HLR_KERNEL_EXP = 1
 HLR_KERNEL_LAPLACE = 2
 HLR_KERNEL_MATERN15 = 3

@@ -3,6 +3,7 @@
 // computed by the compressed H-matrix-vector kernels (Section 5.4).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <string>
 
@@ -90,8 +91,14 @@ __global__ void k_residual(const double *__restrict__ b, double *__restrict__ Ax
     Ax[i] = b[i] - Ax[i];
 }
 
+// x += d
+__global__ void k_add(double *__restrict__ x, const double *__restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    x[i] += d[i];
+}
+
 struct CgWork {
-  double *r, *p, *Ap, *partial, *scal;
+  double *r, *p, *Ap, *rt, *d, *partial, *scal;
 };
 
 int ck(cudaError_t e, const char *what) {
@@ -103,7 +110,7 @@ int ck(cudaError_t e, const char *what) {
 
 int cg_workspace(Handle &H, void **ws) {
   const size_t n = size_t(H.L.n);
-  const size_t bytes = 8 * (3 * n + kDotBlocks + S_N) + 1024;
+  const size_t bytes = 8 * (5 * n + kDotBlocks + S_N) + 1024;
   if (!H.cg_ws) {
     if (cudaMalloc(&H.cg_ws, bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -115,6 +122,77 @@ int cg_workspace(Handle &H, void **ws) {
   return HLR_OK;
 }
 
+namespace {
+
+struct Cg {
+  Handle &H;
+  CgWork W;
+  int64_t n;
+  cudaStream_t st;
+  double h_scal[S_N];
+
+  void dot(const double *a, const double *c, int slot) {
+    k_dot<<<kDotBlocks, kDotThreads, 0, st>>>(a, c, n, W.partial);
+    k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + slot);
+  }
+  int fetch() {
+    int rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg");
+    if (!rc) rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg");
+    return rc;
+  }
+  // ||rhs - A sol|| with the FP64-accumulation product; the residual is left in W.rt
+  int true_residual(const double *rhs, const double *sol, double *norm) {
+    int rc = ck(cudaMemsetAsync(W.rt, 0, 8 * size_t(n), st), "hlr_solve_cg");
+    if (!rc) rc = launch_matvec(H, sol, W.rt, HLR_ACC_FP64, st);
+    if (rc) return rc;
+    k_residual<<<2 * kDotBlocks, 256, 0, st>>>(rhs, W.rt, n);
+    dot(W.rt, W.rt, S_TMP);
+    if ((rc = fetch())) return rc;
+    *norm = std::sqrt(h_scal[S_TMP]);
+    return HLR_OK;
+  }
+  // CG iterations for A sol = rhs with products of accumulation `acc`, from sol (zero_start: from
+  // sol = 0, which is set here), until ||r|| <= stop or `maxit` iterations.
+  int run(const double *rhs, double *sol, bool zero_start, double stop, int maxit, int acc, int *its, bool *conv) {
+    int rc = ck(cudaMemsetAsync(W.Ap, 0, 8 * size_t(n), st), "hlr_solve_cg");
+    if (rc) return rc;
+    if (zero_start) {
+      if ((rc = ck(cudaMemsetAsync(sol, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
+    } else if ((rc = launch_matvec(H, sol, W.Ap, acc, st))) {
+      return rc;
+    }
+    k_init<<<2 * kDotBlocks, 256, 0, st>>>(rhs, W.r, W.p, W.Ap, n);
+    dot(W.r, W.r, S_RR);
+    if ((rc = fetch())) return rc;
+    double rr = h_scal[S_RR];
+    int it = 0;
+    bool ok = std::sqrt(rr) <= stop;
+    while (!ok && it < maxit) {
+      if ((rc = launch_matvec(H, W.p, W.Ap, acc, st))) return rc;
+      dot(W.p, W.Ap, S_PAP);
+      k_update_xr<<<kDotBlocks, kDotThreads, 0, st>>>(sol, W.r, W.p, W.Ap, W.scal, n, W.partial);
+      k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + S_RRNEW);
+      k_update_p<<<2 * kDotBlocks, 256, 0, st>>>(W.p, W.r, W.Ap, W.scal, n);
+      k_copy_scalar<<<1, 1, 0, st>>>(W.scal, S_RR, S_RRNEW);
+      if ((rc = fetch())) return rc;
+      rr = h_scal[S_RR];
+      ++it;
+      if (!std::isfinite(rr)) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: breakdown (non-finite residual)");
+      ok = std::sqrt(rr) <= stop;
+    }
+    *its = it;
+    *conv = ok;
+    return HLR_OK;
+  }
+};
+
+}  // namespace
+
+// HLR_ACC_FP64: one CG run with FP64-accumulation products.
+// HLR_ACC_FP32: iterative refinement. The true residual r = b - A~ x is formed with the FP64
+// product; CG with the (about 7x faster) FP32-accumulation product solves A~ d = r to a relative
+// 1e-3 (or to what the final step still needs), x += d, repeat. Every correction starts from
+// d = 0, so the error of the FP32 products only limits how much one step gains.
 int solve_cg(Handle &H, const double *b, double *x, double rtol, int maxit, int flags, void *stream, int *iters,
              double *relres) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -123,49 +201,39 @@ int solve_cg(Handle &H, const double *b, double *x, double rtol, int maxit, int 
   if (rc) return rc;
   const int64_t n = H.L.n;
   double *base = static_cast<double *>(ws);
-  CgWork W{base, base + n, base + 2 * n, base + 3 * n, base + 3 * n + kDotBlocks};
-  const int gv = 2 * kDotBlocks;
-  double h_scal[S_N];
-  auto dot = [&](const double *a, const double *c, int slot) {
-    k_dot<<<kDotBlocks, kDotThreads, 0, st>>>(a, c, n, W.partial);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + slot);
-  };
-  // Ap = A x ; r = b - Ap ; p = r
-  if ((rc = ck(cudaMemsetAsync(W.Ap, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
-  if ((rc = launch_matvec(H, x, W.Ap, flags, st))) return rc;
-  k_init<<<gv, 256, 0, st>>>(b, W.r, W.p, W.Ap, n);
-  dot(b, b, S_BB);
-  dot(W.r, W.r, S_RR);
-  if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
-  if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
-  const double bnorm = std::sqrt(h_scal[S_BB]);
-  double rr = h_scal[S_RR];
-  int it = 0;
-  bool conv = bnorm == 0.0 || std::sqrt(rr) <= rtol * bnorm;
-  while (!conv && it < maxit) {
-    if ((rc = launch_matvec(H, W.p, W.Ap, flags, st))) return rc;
-    dot(W.p, W.Ap, S_PAP);
-    k_update_xr<<<kDotBlocks, kDotThreads, 0, st>>>(x, W.r, W.p, W.Ap, W.scal, n, W.partial);
-    k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + S_RRNEW);
-    k_update_p<<<gv, 256, 0, st>>>(W.p, W.r, W.Ap, W.scal, n);
-    k_copy_scalar<<<1, 1, 0, st>>>(W.scal, S_RR, S_RRNEW);
-    if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
-    if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
-    rr = h_scal[S_RR];
-    ++it;
-    if (!std::isfinite(rr)) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: breakdown (non-finite residual)");
-    conv = std::sqrt(rr) <= rtol * bnorm;
+  Cg cg{H, CgWork{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 5 * n + kDotBlocks},
+        n, st, {}};
+  cg.dot(b, b, S_BB);
+  if ((rc = cg.fetch())) return rc;
+  const double bnorm = std::sqrt(cg.h_scal[S_BB]);
+  int total = 0;
+  double rnorm = 0.0;
+  if (bnorm == 0.0) {
+    if ((rc = cg.true_residual(b, x, &rnorm))) return rc;
+  } else if (flags == HLR_ACC_FP64) {
+    int it = 0;
+    bool conv = false;
+    if ((rc = cg.run(b, x, false, rtol * bnorm, maxit, HLR_ACC_FP64, &it, &conv))) return rc;
+    total = it;
+    if ((rc = cg.true_residual(b, x, &rnorm))) return rc;
+  } else {
+    if ((rc = cg.true_residual(b, x, &rnorm))) return rc;
+    for (int outer = 0; rnorm > rtol * bnorm && total < maxit && outer < 64; ++outer) {
+      const double eta = std::max(0.1 * rtol * bnorm / rnorm, 1e-3);
+      int it = 0;
+      bool conv = false;
+      // W.rt holds the true residual, the right-hand side of the correction equation A~ d = r
+      // (run() reads it once, in k_init, and never writes it)
+      if ((rc = cg.run(cg.W.rt, cg.W.d, true, eta * rnorm, maxit - total, HLR_ACC_FP32, &it, &conv))) return rc;
+      total += it;
+      k_add<<<2 * kDotBlocks, 256, 0, st>>>(x, cg.W.d, n);
+      if ((rc = cg.true_residual(b, x, &rnorm))) return rc;
+      if (it == 0) break;
+    }
   }
-  // true residual of the returned x
-  if ((rc = ck(cudaMemsetAsync(W.Ap, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
-  if ((rc = launch_matvec(H, x, W.Ap, flags, st))) return rc;
-  k_residual<<<gv, 256, 0, st>>>(b, W.Ap, n);
-  dot(W.Ap, W.Ap, S_TMP);
-  if ((rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg"))) return rc;
-  if ((rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg"))) return rc;
-  if (iters) *iters = it;
-  if (relres) *relres = bnorm > 0 ? std::sqrt(h_scal[S_TMP]) / bnorm : 0.0;
-  if (!conv) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: maxit reached");
+  if (iters) *iters = total;
+  if (relres) *relres = bnorm > 0 ? rnorm / bnorm : 0.0;
+  if (bnorm > 0 && !(rnorm <= rtol * bnorm)) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: maxit reached");
   return HLR_OK;
 }
 
@@ -187,7 +255,9 @@ extern "C" int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *
                                   void *stream) {
   if (nreq < 0 || (nreq > 0 && (!h || !nrhs || !X || !ldx || !Y || !ldy)))
     return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad arguments");
-  if (flags != HLR_ACC_FP64 && flags != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad flags");
+  const int acc = flags & ~HLR_MULTI;
+  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags & HLR_MULTI) && acc != HLR_ACC_FP32))
+    return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad flags");
   for (int q = 0; q < nreq; ++q) {
     Handle *H = lookup(h[q]);
     if (!H) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: unknown handle");

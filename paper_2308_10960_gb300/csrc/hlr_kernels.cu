@@ -1190,16 +1190,17 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
     if (H[q]->device != dev) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: handles of different devices");
   props(dev);
   const bool fp32 = (flags & 0xff) == HLR_ACC_FP32;
+  const int multi_from = (flags & HLR_MULTI) ? 1 : 2;  // fewest columns that take the multi-RHS kernels
   Batcher<FMT_AFL32, 1> b32(st);
   Batcher<FMT_AFL64, 1> b64(st);
   Batcher<FMT_RAW64, 1> braw(st);
   Batcher<FMT_AFL32, kRB> bm(st);
   // pass scratch first (growing it frees the old one, which no pending product may still use)
   for (int q = 0; q < nreq; ++q) {
-    if (nrhs[q] <= 1 || !fp32 || H[q]->L.raw) continue;
+    if (nrhs[q] < multi_from || !fp32 || H[q]->L.raw) continue;
     int passes = 0;
     for (int k = 0; k < nreq; ++k)
-      if (H[k] == H[q] && nrhs[k] > 1) passes = std::max(passes, (nrhs[k] + kRB - 1) / kRB);
+      if (H[k] == H[q] && nrhs[k] >= multi_from) passes = std::max(passes, (nrhs[k] + kRB - 1) / kRB);
     float *xp, *tw;
     double *part;
     size_t stride;
@@ -1209,7 +1210,7 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
     Handle &Hq = *H[q];
     const int r = nrhs[q];
     if (r <= 0) continue;
-    if (r > 1 && fp32 && !Hq.L.raw) {
+    if (r >= multi_from && fp32 && !Hq.L.raw) {
       const int passes = (r + kRB - 1) / kRB;
       float *xp, *tw;
       double *part;
