@@ -41,12 +41,12 @@ enum : uint8_t { PF_START_LEAF = 1, PF_END_LEAF = 2 };
 
 struct PieceHdr {
   uint16_t nseg;
-  uint16_t ncols;    // column slices in the piece (<= kMaxCols)
+  uint16_t ncols;    // column slices (lanes) in the piece (<= kMaxCols)
   uint16_t nr;       // phase 2: rows of the leaf
   uint8_t flags;     // PF_START_LEAF, PF_END_LEAF (phase 2)
   uint8_t pad0;
   uint32_t row0;     // phase 2: first row of the leaf (cluster order)
-  uint32_t pad1;
+  uint8_t h[4];      // bank-column pieces: words per lane column in the region of warp 0..3
 };
 static_assert(sizeof(PieceHdr) == 16, "PieceHdr");
 
@@ -82,6 +82,23 @@ struct Seg {
   };
 };
 static_assert(sizeof(Seg) == 32, "Seg");
+
+// Bank-column pieces (the AFL formats). After the segments come one LaneHdr per lane and then
+// the data as four warp regions: region w is an array of h[w] rows of 32 words, and lane
+// t = 32 w + l owns column l of it, so its k-th word is at region + 32 k + l. A warp's 32 lanes
+// thus read 32 different shared-memory banks whatever their positions in their slices. Each
+// lane column holds one slice from bit 0 (value r at bits [r w, r w + w)). Lanes are ordered by
+// slice length (X: whole aligned groups of 2^lg lanes) so that the columns of a warp are about
+// equally long. An X column of an item of nr rows is read by G = 2^lg lanes (the smallest G
+// with 64 G >= nr), lane g of the group taking rows g, g + G, g + 2G, ... (value i of its
+// column is row g + i G). The FP64 format keeps the contiguous layout (ColHdr below).
+struct LaneHdr {
+  uint8_t seg;       // segment of the lane's slice (0xff: idle lane)
+  uint8_t j;         // column of the slice within its segment
+  uint8_t e, m;      // AFL parameters of the slice's unit
+};
+static_assert(sizeof(LaneHdr) == 4, "LaneHdr");
+constexpr uint64_t kStridedSlice = uint64_t(1) << 62;  // decode map: slice stored as a lane column
 
 // Column header of a W or X slice: word offset from the segment data start, e, m.
 struct ColHdr {

@@ -78,20 +78,30 @@ struct Jobs {
 };
 static_assert(sizeof(Jobs<kMaxBatch>) < 30000, "kernel parameter size");
 
-// ring slot: piece, 16-byte pad, staged multipliers (phase 1 stages more: x of the items' rows);
-// the multi-RHS kernels read their multipliers from global memory and stage none
+// ring slot: piece, pad, staged multipliers (phase 1 stages more: x of the items' rows); the
+// multi-RHS kernels read their multipliers from global memory and stage none. The pad covers
+// the words a lane reads past its column (at most two rows of 32 words beyond the last region).
+constexpr size_t kSlotPad = 272;
 template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t slot_bytes() {
-  return size_t(kPieceMax) + 16 + (R == 1 ? size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz : 0);
+  return size_t(kPieceMax) + kSlotPad + (R == 1 ? size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz : 0);
 }
-// dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers and the
-// FP32 path its transposition tiles (multi-RHS: one buffer of kRB sums per row and warp)
+// phase-2 transposition tiles of one warp: 16 rows x 33 (single RHS, accumulation type) or
+// kRB x 4 rows x 33 floats (multi-RHS)
+template <int FMT, int R>
+__host__ __device__ constexpr size_t tile_bytes() {
+  return R > 1 ? size_t(kRB) * 4 * 33 * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
+}
+// dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers (single RHS:
+// two halves; multi-RHS: kRB sums per row and warp, sharing the space of the tiles)
 template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
   return size_t(kStages) * slot_bytes<FMT, PH, R>() + 2 * kStages * 8 + 16 +
          (PH == 0 ? 0
-          : R > 1 ? size_t(kCWarps) * 64 * kRB * 8 + size_t(kCWarps) * 32 * kRB * 4
-                  : 2 * kCWarps * 64 * 8 + (FMT == 0 ? size_t(kCWarps) * 16 * 33 * 4 : 0));
+          : R > 1 ? (size_t(kCWarps) * tile_bytes<FMT, R>() > size_t(kCWarps) * 64 * kRB * 8
+                         ? size_t(kCWarps) * tile_bytes<FMT, R>()
+                         : size_t(kCWarps) * 64 * kRB * 8)
+                  : 2 * kCWarps * 64 * 8 + size_t(kCWarps) * tile_bytes<FMT, R>());
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -204,6 +214,30 @@ __device__ __forceinline__ uint64_t code64_at(const uint32_t *p, uint32_t bit) {
   return (uint64_t(__funnelshift_r(b, c, bit)) << 32) | __funnelshift_r(a, b, bit);
 }
 
+// Bank-column pieces: first word of the column of lane t, and codes of the column (word k of
+// the column is col[32 k]).
+__device__ __forceinline__ uint32_t bc_column(const PieceHdr *ph, int t) {
+  const uint32_t hdr_w = (16u + 32u * ph->nseg + ((4u * ph->ncols + 15u) & ~15u)) / 4u;
+  const int w = t >> 5;
+  uint32_t rows = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (k < w) rows += ph->h[k];
+  return hdr_w + 32u * rows + uint32_t(t & 31);
+}
+__device__ __forceinline__ uint32_t bc_code32(const uint32_t *col, uint32_t bit) {
+  const uint32_t q = bit >> 5;
+  return __funnelshift_r(col[32 * q], col[32 * q + 32], bit);
+}
+__device__ __forceinline__ uint64_t bc_code64(const uint32_t *col, uint32_t bit) {
+  const uint32_t q = bit >> 5;
+  const uint32_t a = col[32 * q], b = col[32 * q + 32], c = col[32 * q + 64];
+  return (uint64_t(__funnelshift_r(b, c, bit)) << 32) | __funnelshift_r(a, b, bit);
+}
+__device__ __forceinline__ const LaneHdr *lane_hdrs(const uint8_t *slot, const PieceHdr *ph) {
+  return reinterpret_cast<const LaneHdr *>(slot + 16 + 32 * size_t(ph->nseg));
+}
+
 // Value r of a slice (FP32 / FP64 accumulation types) for the generic (wide) path.
 template <typename A>
 __device__ __forceinline__ A dec_at(const uint32_t *p, uint32_t bit, const ColDec &c) {
@@ -314,7 +348,7 @@ __device__ bool produce(const DevLayout &L, uint32_t e0, uint32_t e1, uint8_t *s
       } else if (R == 1 && lane == 0) {
         const uint32_t nelem = b & 0xffffu, which = b >> 16;
         const uint8_t *src = (which == 0 ? xsrc : which == 1 ? tsrc : fsrc) + size_t(a) * esz;
-        tma_load(smem + size_t(cur) * slot + kPieceMax + 16 + size_t(c) * esz, src, nelem * esz, &full[cur]);
+        tma_load(smem + size_t(cur) * slot + kPieceMax + kSlotPad + size_t(c) * esz, src, nelem * esz, &full[cur]);
       }
     }
   }
@@ -373,7 +407,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
-    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + 16);
+    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + kSlotPad);
     const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
     const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
     A dot = A(0);
@@ -382,41 +416,58 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
     int j = 0;
     bool lead = false;
     if (t < int(ph->ncols)) {
-      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
-      const int rel = t - int(sg.cstart);
-      const int jj = rel >> sg.lg;
-      if (jj < int(sg.nc)) {
-        sgp = &sg;
-        j = jj;
-        G = 1u << sg.lg;
-        const int sub = rel & int(G - 1);
-        lead = sub == 0;
-        const uint32_t ch = Wd[sg.col_w + j];
-        const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
-        const int r0 = sub * kSubRows;
-        const int rc = min(kSubRows, int(sg.nr) - r0);  // rows of this lane (may be <= 0)
-        const A *xr = aux + sg.xs + r0;
-        if constexpr (FMT == FMT_RAW64) {
+      if constexpr (FMT == FMT_RAW64) {
+        // contiguous pieces: the lane's segment by binary search over the segments' first lanes
+        const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
+        const int rel = t - int(sg.cstart);
+        const int jj = rel >> sg.lg;
+        if (jj < int(sg.nc)) {
+          sgp = &sg;
+          j = jj;
+          G = 1u << sg.lg;
+          const int sub = rel & int(G - 1);
+          lead = sub == 0;
+          const uint32_t ch = Wd[sg.col_w + j];
+          const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
+          const int r0 = sub * kSubRows;
+          const int rc = min(kSubRows, int(sg.nr) - r0);  // rows of this lane (may be <= 0)
+          const A *xr = aux + sg.xs + r0;
           const double *Dd = reinterpret_cast<const double *>(Dc) + r0;
 #pragma unroll 4
           for (int r = 0; r < rc; ++r) dot = fma(Dd[r], xr[r], dot);
-        } else {
-          const ColDec c = col_dec((ch >> 16) & 0xffu, ch >> 24);
+        }
+      } else {
+        // bank-column pieces: the lane's slice is column (t & 31) of its warp's region; value i
+        // of it is row sub + i G of the X column
+        const LaneHdr h = lane_hdrs(sl, ph)[t];
+        if (h.seg != 0xff) {
+          const Seg &sg = segs[h.seg];
+          sgp = &sg;
+          j = h.j;
+          G = 1u << sg.lg;
+          const int sub = t & int(G - 1);
+          lead = sub == 0;
+          const int rc = (int(sg.nr) - sub + int(G) - 1) >> sg.lg;
+          const A *xr = aux + sg.xs + sub;
+          const int xs = int(G);
+          const uint32_t *col = Wd + bc_column(ph, t);
+          const ColDec c = col_dec(h.e, h.m);
           if (c.narrow) {
-            uint32_t bit = uint32_t(r0) * c.w;
+            uint32_t bit = 0;
             if constexpr (FMT == FMT_AFL32) {
               if (c.fast32) {
 #pragma unroll 8
-                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(dec_f32(code32_at(Dc, bit), c), xr[r], dot);
+                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(dec_f32(bc_code32(col, bit), c), xr[r * xs], dot);
               } else {
-                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(float(dec_f64(code32_at(Dc, bit), c)), xr[r], dot);
+                for (int r = 0; r < rc; ++r, bit += c.w)
+                  dot = fmaf(float(dec_f64(bc_code32(col, bit), c)), xr[r * xs], dot);
               }
             } else {
 #pragma unroll 4
-              for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(code32_at(Dc, bit), c), xr[r], dot);
+              for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(bc_code32(col, bit), c), xr[r * xs], dot);
             }
           } else {
-            for (int r = 0; r < rc; ++r) dot += dec_at<A>(Dc, uint32_t(r0 + r) * c.w, c) * xr[r];
+            for (int r = 0; r < rc; ++r) dot += A(dec_f64(bc_code64(col, uint32_t(r) * c.w), c)) * xr[r * xs];
           }
         }
       }
@@ -492,20 +543,39 @@ __device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const 
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phase 2 consumers, FP32 path: one lane per column slice of the leaf; every 32 rows the lanes
-// write their products to a padded shared-memory tile and sum it transposed (a lane per row)
+// Phase 2, FP32 accumulation: one lane per column slice of the leaf (its lane column of the
+// bank-column piece). A lane keeps the FP32 sums of its columns' products for all rows of the
+// leaf in registers, over all pieces of the leaf; at the end of the leaf each warp reduces its
+// 32 lanes' row sums with a butterfly of shuffles (fixed order) and the four warps' sums are
+// added in FP64, in fixed order, into y.
 // ---------------------------------------------------------------------------------------------
-template <int FMT>
-__device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
-                               uint64_t *empty, double *red, float *tiles, double *__restrict__ y,
-                               uint32_t &parity) {
-  using A = typename Tr<FMT>::A;
-  constexpr size_t slot = slot_bytes<FMT, 1>();
+// rows [0, nr) of the lane's slice into acc[r]; rows past the leaf decode the slice's first value
+// (in bounds) and are dropped. GEN: the generic FP64 decode (wide codes, large e or m).
+template <bool GEN>
+__device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t *col, const ColDec &c, float mult) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (16 * k >= nr) break;
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      const int r = 16 * k + rr;
+      const bool ok = r < nr;
+      const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
+      const float p = GEN ? float(dec_f64(bc_code64(col, bit), c)) * mult : dec_mul_f32(bc_code32(col, bit), c, mult);
+      if (ok) acc[r] += p;
+    }
+  }
+}
+
+__device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                   uint64_t *empty, double *red, double *__restrict__ y, uint32_t &parity) {
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  Comp32 acc[4];  // rows lane + 16 k (lanes 0..15) of the leaf: this warp's columns so far
+  float acc[64];
+#pragma unroll
+  for (int r = 0; r < 64; ++r) acc[r] = 0.f;
   int64_t gi = 0;
   double yold = 0.0;  // y of this thread's row, read when the leaf starts
-  float *tile = tiles + warp * (16 * 33);
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -514,7 +584,99 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
-    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + 16);
+    const float *aux = reinterpret_cast<const float *>(sl + kPieceMax + kSlotPad);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+#pragma unroll
+      for (int r = 0; r < 64; ++r) acc[r] = 0.f;
+      if (t < nr) {
+        gi = __ldg(L.perm + ph->row0 + uint32_t(t));
+        yold = y[gi];
+      }
+    }
+    // idle lanes decode e = m = 0 codes (value 0) times a zero multiplier from the header words
+    float mult = 0.f;
+    uint32_t e = 0, m = 0;
+    const uint32_t *col = Wd;
+    if (t < int(ph->ncols)) {
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
+        mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * float(sg.m_min) : aux[sg.xs + h.j];
+        e = h.e;
+        m = h.m;
+        col = Wd + bc_column(ph, t);
+      }
+    }
+    const ColDec c = col_dec(e, m);
+    if (__all_sync(kFull, c.fast32))  // the FP32 bit-pattern decode for the whole warp
+      p2_rows<false>(acc, nr, col, c, mult);
+    else
+      p2_rows<true>(acc, nr, col, c, mult);
+    if (flags & PF_END_LEAF) {
+      // reduce-scatter over the warp: 5 halving stages (stage s keeps the upper half of the
+      // vector when lane bit 4 - s is set); afterwards lane l holds the sums of rows 2l, 2l + 1
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        const int half = 32 >> st;      // current vector length / 2
+        const int mask = 16 >> st;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+          const float send = up ? acc[q] : acc[q + half];
+          const float keep = up ? acc[q + half] : acc[q];
+          acc[q] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+      }
+      const int rb = 2 * lane;
+      double *buf = red + parity * (kCWarps * 64);
+      buf[warp * 64 + rb] = double(acc[0]);
+      buf[warp * 64 + rb + 1] = double(acc[1]);
+      bar_consumers();
+      if (t < nr) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kCWarps; ++w) sum += buf[w * 64 + t];
+        y[gi] = yold + sum;  // the only update of this row (its leaf has one owner CTA)
+      }
+      parity ^= 1u;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase 2 consumers, AFL formats: one lane per column slice of the leaf (its lane column of the
+// bank-column piece); every 16 rows the lanes write their products to a padded shared-memory
+// tile and sum it transposed (two lanes per row, one shuffle). FP32 path: FP32 products and
+// tile sums, compensated FP32 pairs across pieces; FP64 path: the same in FP64.
+// ---------------------------------------------------------------------------------------------
+template <int FMT>
+__device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                               uint64_t *empty, double *red, typename Tr<FMT>::A *tiles, double *__restrict__ y,
+                               uint32_t &parity) {
+  using A = typename Tr<FMT>::A;
+  using Acc = typename std::conditional<FMT == FMT_AFL32, Comp32, Sum64>::type;
+  constexpr size_t slot = slot_bytes<FMT, 1>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  Acc acc[4];  // rows lane + 16 k (lanes 0..15) of the leaf: this warp's columns so far
+  int64_t gi = 0;
+  double yold = 0.0;  // y of this thread's row, read when the leaf starts
+  A *tile = tiles + warp * (16 * 33);
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const A *aux = reinterpret_cast<const A *>(sl + kPieceMax + kSlotPad);
     const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
     const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
     const int nr = ph->nr;
@@ -527,11 +689,19 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
         yold = y[gi];
       }
     }
+    // idle lanes decode e = m = 0 codes (value 0) times a zero multiplier from the header words
     A mult = A(0);
-    uint32_t start = 0, e = 0, m = 0;
+    uint32_t e = 0, m = 0;
+    const uint32_t *col = Wd;
     if (t < int(ph->ncols)) {
-      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
-      slice_setup<FMT>(sg, t - int(sg.cstart), nr, Wd, aux, start, e, m, mult);
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
+        mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * A(sg.m_min) : aux[sg.xs + h.j];
+        e = h.e;
+        m = h.m;
+        col = Wd + bc_column(ph, t);
+      }
     }
     const ColDec c = col_dec(e, m);
 #pragma unroll
@@ -539,26 +709,35 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
       const int r0 = 16 * k;
       if (r0 >= nr) break;
       const int rows = min(16, nr - r0);
-      const uint32_t bit0 = start + uint32_t(r0) * c.w;
-      if (rows == 16 && c.fast32) {
+      const uint32_t bit0 = uint32_t(r0) * c.w;
+      if constexpr (FMT == FMT_AFL32) {
+        if (rows == 16 && c.fast32) {
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) tile[rr * 33 + lane] = dec_mul_f32(code32_at(Wd, bit0 + rr * c.w), c, mult);
-      } else if (c.fast32) {
-        for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_mul_f32(code32_at(Wd, bit0 + rr * c.w), c, mult);
-      } else if (c.narrow) {
-        for (int rr = 0; rr < rows; ++rr)
-          tile[rr * 33 + lane] = float(dec_f64(code32_at(Wd, bit0 + rr * c.w), c)) * mult;
+          for (int rr = 0; rr < 16; ++rr) tile[rr * 33 + lane] = dec_mul_f32(bc_code32(col, bit0 + rr * c.w), c, mult);
+        } else if (c.fast32) {
+          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_mul_f32(bc_code32(col, bit0 + rr * c.w), c, mult);
+        } else if (c.narrow) {
+          for (int rr = 0; rr < rows; ++rr)
+            tile[rr * 33 + lane] = float(dec_f64(bc_code32(col, bit0 + rr * c.w), c)) * mult;
+        } else {
+          for (int rr = 0; rr < rows; ++rr)
+            tile[rr * 33 + lane] = float(dec_f64(bc_code64(col, bit0 + rr * c.w), c)) * mult;
+        }
       } else {
-        for (int rr = 0; rr < rows; ++rr)
-          tile[rr * 33 + lane] = float(dec_f64(code64_at(Wd, start + uint32_t(r0 + rr) * c.w), c)) * mult;
+        if (c.narrow) {
+#pragma unroll 4
+          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_f64(bc_code32(col, bit0 + rr * c.w), c) * mult;
+        } else {
+          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_f64(bc_code64(col, bit0 + rr * c.w), c) * mult;
+        }
       }
       __syncwarp();
       // transposed sum: lane l adds row (l & 15) over columns 16 (l >> 4) .. + 15; the two
       // halves are combined with one shuffle
       const int row = lane & 15;
-      float sum = 0.f;
+      A sum = A(0);
       if (row < rows) {
-        const float *tr = tile + row * 33 + (lane >> 4) * 16;
+        const A *tr = tile + row * 33 + (lane >> 4) * 16;
 #pragma unroll
         for (int cc = 0; cc < 16; ++cc) sum += tr[cc];
       }
@@ -609,7 +788,7 @@ __device__ bool consume_phase2_rows(const DevLayout &L, uint32_t np, uint32_t &i
     }
     const uint8_t *sl = smem + size_t(s) * slot;
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
-    const double *aux = reinterpret_cast<const double *>(sl + kPieceMax + 16);
+    const double *aux = reinterpret_cast<const double *>(sl + kPieceMax + kSlotPad);
     const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
     const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
     const int nr = ph->nr;
@@ -686,37 +865,35 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
     int j = 0;
     bool lead = false;
     if (t < int(ph->ncols)) {
-      const Seg &sg = segs[find_seg(segs, ph->nseg, t)];
-      const int rel = t - int(sg.cstart);
-      const int jj = rel >> sg.lg;
-      if (jj < int(sg.nc)) {
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
         sgp = &sg;
-        j = jj;
+        j = h.j;
         G = 1u << sg.lg;
-        const int sub = rel & int(G - 1);
+        const int sub = t & int(G - 1);
         lead = sub == 0;
-        const uint32_t ch = Wd[sg.col_w + j];
-        const uint32_t *Dc = Wd + sg.data_w + (ch & 0xffffu);
-        const int r0 = sub * kSubRows;
-        const int rc = min(kSubRows, int(sg.nr) - r0);
-        const float4 *xr = xp4 + (size_t(sg.gx) + r0) * (kRB / 4);
-        const ColDec c = col_dec((ch >> 16) & 0xffu, ch >> 24);
+        const int rc = (int(sg.nr) - sub + int(G) - 1) >> sg.lg;   // rows sub, sub + G, ...
+        const float4 *xr = xp4 + (size_t(sg.gx) + sub) * (kRB / 4);
+        const int xs = int(G) * (kRB / 4);
+        const uint32_t *col = Wd + bc_column(ph, t);
+        const ColDec c = col_dec(h.e, h.m);
 #pragma unroll 4
         for (int r = 0; r < rc; ++r) {
           float v;
           if (c.fast32)
-            v = dec_f32(code32_at(Dc, uint32_t(r0 + r) * c.w), c);
+            v = dec_f32(bc_code32(col, uint32_t(r) * c.w), c);
           else if (c.narrow)
-            v = float(dec_f64(code32_at(Dc, uint32_t(r0 + r) * c.w), c));
+            v = float(dec_f64(bc_code32(col, uint32_t(r) * c.w), c));
           else
-            v = float(dec_f64(code64_at(Dc, uint32_t(r0 + r) * c.w), c));
+            v = float(dec_f64(bc_code64(col, uint32_t(r) * c.w), c));
 #pragma unroll
-          for (int h = 0; h < kRB / 4; ++h) {
-            const float4 xv = __ldg(xr + r * (kRB / 4) + h);
-            acc[4 * h] = fmaf(v, xv.x, acc[4 * h]);
-            acc[4 * h + 1] = fmaf(v, xv.y, acc[4 * h + 1]);
-            acc[4 * h + 2] = fmaf(v, xv.z, acc[4 * h + 2]);
-            acc[4 * h + 3] = fmaf(v, xv.w, acc[4 * h + 3]);
+          for (int hh = 0; hh < kRB / 4; ++hh) {
+            const float4 xv = __ldg(xr + r * xs + hh);
+            acc[4 * hh] = fmaf(v, xv.x, acc[4 * hh]);
+            acc[4 * hh + 1] = fmaf(v, xv.y, acc[4 * hh + 1]);
+            acc[4 * hh + 2] = fmaf(v, xv.z, acc[4 * hh + 2]);
+            acc[4 * hh + 3] = fmaf(v, xv.w, acc[4 * hh + 3]);
           }
         }
       }
@@ -736,8 +913,8 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
         const float f = __ldg(L.fac32 + sg.tidx + j);
         float4 *dst = reinterpret_cast<float4 *>(jb.tw + (size_t(sg.tidx) + j) * kRB);
 #pragma unroll
-        for (int h = 0; h < kRB / 4; ++h)
-          dst[h] = make_float4(acc[4 * h] * f, acc[4 * h + 1] * f, acc[4 * h + 2] * f, acc[4 * h + 3] * f);
+        for (int hh = 0; hh < kRB / 4; ++hh)
+          dst[hh] = make_float4(acc[4 * hh] * f, acc[4 * hh + 1] * f, acc[4 * hh + 2] * f, acc[4 * hh + 3] * f);
       } else {
         double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * kRB;
 #pragma unroll
@@ -751,20 +928,24 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 2 (FP32): lanes are the rows of the leaf (lane, lane + 32), the warps
-// take the piece's column slices in turn; a value is decoded once and multiplied by the kRB
-// multipliers of its column (t m_min(W) of the pass, or X row times m_min for dense blocks).
-// FP32 sums over the <= 32 columns a warp takes from one piece, compensated FP32 pairs across
-// pieces, FP64 for the sum over warps and into Y.
+// Multi-RHS pass, phase 2 (FP32): one lane per column slice (its bank column); a value is decoded
+// once and multiplied by the kRB multipliers of its column (t m_min(W) of the pass, or the X row
+// of the column times m_min). Every 4 rows the lanes write their kRB x 4 products to a padded
+// tile and lane i sums row 4k + (i & 3) of right-hand side i >> 2 over the 32 columns; FP32 sums
+// over the <= 32 columns a warp takes from one piece, compensated FP32 pairs across pieces, FP64
+// for the sum over warps and into Y.
 // ---------------------------------------------------------------------------------------------
 __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
-                                     uint64_t *empty, double *red, float *mbufs) {
+                                     uint64_t *empty, float *tiles) {
   const DevLayout &L = jb.L;
   constexpr size_t slot = slot_bytes<FMT_AFL32, 1, kRB>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
-  Comp32 c0[kRB], c1[kRB];
+  float *tile = tiles + warp * (kRB * 4 * 33);
+  double *red = reinterpret_cast<double *>(tiles);  // used at the end of a leaf, after a barrier
+  const int qi = lane >> 2, ri = lane & 3;           // this lane's (rhs, row) of each 4-row chunk
+  Comp32 acc[16];
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -779,90 +960,67 @@ __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, u
     const uint32_t flags = ph->flags;
     if (flags & PF_START_LEAF) {
 #pragma unroll
-      for (int q = 0; q < kRB; ++q) {
-        c0[q].reset();
-        c1[q].reset();
-      }
+      for (int k = 0; k < 16; ++k) acc[k].reset();
     }
-    float a0[kRB], a1[kRB];
+    float mv[kRB];
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) a0[q] = a1[q] = 0.f;
-    const bool ok0 = lane < nr, ok1 = lane + 32 < nr;
-    const int ncols = ph->ncols, nseg = ph->nseg;
-    // the multipliers of this warp's (<= 32) columns, loaded by one lane each (all loads in
-    // flight together) into the warp's buffer: one global-memory latency per piece
-    float4 *mb = reinterpret_cast<float4 *>(mbufs) + warp * 32 * (kRB / 4);
-    {
-      const int col = warp + kCWarps * lane;
-      if (col < ncols) {
-        const Seg &sg = segs[find_seg(segs, nseg, col)];
-        const int j = col - int(sg.cstart);
+    for (int q = 0; q < kRB; ++q) mv[q] = 0.f;
+    uint32_t e = 0, m = 0;
+    const uint32_t *col = Wd;
+    if (t < int(ph->ncols)) {
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
         float4 lo, hi;
         if (sg.kind == SEG_DENSE) {
           const float mm = float(sg.m_min);
-          const float4 x0 = __ldg(xp4 + (size_t(sg.gx) + j) * (kRB / 4));
-          const float4 x1 = __ldg(xp4 + (size_t(sg.gx) + j) * (kRB / 4) + 1);
+          const float4 x0 = __ldg(xp4 + (size_t(sg.gx) + h.j) * (kRB / 4));
+          const float4 x1 = __ldg(xp4 + (size_t(sg.gx) + h.j) * (kRB / 4) + 1);
           lo = make_float4(x0.x * mm, x0.y * mm, x0.z * mm, x0.w * mm);
           hi = make_float4(x1.x * mm, x1.y * mm, x1.z * mm, x1.w * mm);
         } else {
-          lo = __ldg(tw4 + (size_t(sg.gx) + j) * (kRB / 4));
-          hi = __ldg(tw4 + (size_t(sg.gx) + j) * (kRB / 4) + 1);
+          lo = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4));
+          hi = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4) + 1);
         }
-        mb[lane * 2] = lo;
-        mb[lane * 2 + 1] = hi;
+        mv[0] = lo.x; mv[1] = lo.y; mv[2] = lo.z; mv[3] = lo.w;
+        mv[4] = hi.x; mv[5] = hi.y; mv[6] = hi.z; mv[7] = hi.w;
+        e = h.e;
+        m = h.m;
+        col = Wd + bc_column(ph, t);
       }
     }
-    __syncwarp();
-    int si = 0;
-    for (int col = warp, k = 0; col < ncols; col += kCWarps, ++k) {
-      while (si + 1 < nseg && int(segs[si + 1].cstart) <= col) ++si;
-      const Seg &sg = segs[si];
-      const int j = col - int(sg.cstart);
-      uint32_t start, e, m;
-      if (sg.kind == SEG_DENSE) {
-        e = sg.col_w & 0xffu;
-        m = (sg.col_w >> 8) & 0xffu;
-        start = uint32_t(sg.data_w) * 32u + uint32_t(j * nr) * (1u + e + m);
-      } else {
-        const uint32_t ch = Wd[sg.col_w + j];
-        e = (ch >> 16) & 0xffu;
-        m = ch >> 24;
-        start = (uint32_t(sg.data_w) + (ch & 0xffffu)) * 32u;
-      }
-      const float4 mlo = mb[k * 2], mhi = mb[k * 2 + 1];
-      const ColDec c = col_dec(e, m);
-      float v0 = 0.f, v1 = 0.f;
-      if (c.fast32) {
-        if (ok0) v0 = dec_f32(code32_at(Wd, start + uint32_t(lane) * c.w), c);
-        if (ok1) v1 = dec_f32(code32_at(Wd, start + uint32_t(lane + 32) * c.w), c);
-      } else if (c.narrow) {
-        if (ok0) v0 = float(dec_f64(code32_at(Wd, start + uint32_t(lane) * c.w), c));
-        if (ok1) v1 = float(dec_f64(code32_at(Wd, start + uint32_t(lane + 32) * c.w), c));
-      } else {
-        if (ok0) v0 = float(dec_f64(code64_at(Wd, start + uint32_t(lane) * c.w), c));
-        if (ok1) v1 = float(dec_f64(code64_at(Wd, start + uint32_t(lane + 32) * c.w), c));
-      }
-      const float mv[kRB] = {mlo.x, mlo.y, mlo.z, mlo.w, mhi.x, mhi.y, mhi.z, mhi.w};
+    const ColDec c = col_dec(e, m);
 #pragma unroll
-      for (int q = 0; q < kRB; ++q) {
-        a0[q] = fmaf(v0, mv[q], a0[q]);
-        a1[q] = fmaf(v1, mv[q], a1[q]);
-      }
-    }
-    __syncwarp();  // the multiplier buffer is refilled for the next piece
+    for (int k = 0; k < 16; ++k) {  // 4-row chunks
+      const int r0 = 4 * k;
+      if (r0 >= nr) break;
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) {
-      c0[q].add(a0[q]);
-      c1[q].add(a1[q]);
+      for (int rr = 0; rr < 4; ++rr) {
+        const uint32_t bit = uint32_t(r0 + rr) * c.w;
+        float v = 0.f;
+        if (r0 + rr < nr) {
+          if (c.fast32)
+            v = dec_f32(bc_code32(col, bit), c);
+          else if (c.narrow)
+            v = float(dec_f64(bc_code32(col, bit), c));
+          else
+            v = float(dec_f64(bc_code64(col, bit), c));
+        }
+#pragma unroll
+        for (int q = 0; q < kRB; ++q) tile[(q * 4 + rr) * 33 + lane] = v * mv[q];
+      }
+      __syncwarp();
+      float sum = 0.f;
+      const float *tr = tile + lane * 33;  // row (qi, ri) of the tile is row `lane`
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) sum += tr[cc];
+      acc[k].add(sum);
+      __syncwarp();
     }
     if (flags & PF_END_LEAF) {
-      // per-warp row sums of the kRB right-hand sides, then per (row, rhs) the sum over the
-      // warps in fixed order; the buffer is reused only after a second barrier
+      bar_consumers();  // every warp is done with its tile before the sums reuse the space
 #pragma unroll
-      for (int q = 0; q < kRB; ++q) {
-        red[(warp * 64 + lane) * kRB + q] = c0[q].value();
-        red[(warp * 64 + lane + 32) * kRB + q] = c1[q].value();
-      }
+      for (int k = 0; k < 16; ++k) red[(warp * 64 + 4 * k + ri) * kRB + qi] = acc[k].value();
       bar_consumers();
       const uint32_t row0 = ph->row0;
       for (int idx = t; idx < nr * jb.nrhs; idx += kConsumers) {
@@ -885,13 +1043,14 @@ __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, u
 // range of each product's piece stream in turn; the ring slots and their mbarrier phases run on
 // across products.
 template <int FMT, int PH, int R, int NB>
-__global__ void __launch_bounds__(kThreads) k_product(const __grid_constant__ Jobs<NB> J) {
+__global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__ Jobs<NB> J) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr size_t slot = slot_bytes<FMT, PH, R>();
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
   uint64_t *empty = full + kStages;
   double *red = reinterpret_cast<double *>(empty + kStages);
-  float *tiles = reinterpret_cast<float *>(red + 2 * kCWarps * 64);
+  using A = typename Tr<FMT>::A;
+  A *tiles = reinterpret_cast<A *>(red + 2 * kCWarps * 64);
   uint32_t np_all = 0;
   for (int m = 0; m < J.n; ++m) np_all += __ldg(J.j[m].L.ph[PH].cta_np + blockIdx.x);
   if (threadIdx.x == 0) {
@@ -916,11 +1075,12 @@ __global__ void __launch_bounds__(kThreads) k_product(const __grid_constant__ Jo
       if constexpr (PH == 0)
         ok = consume_phase1_multi(jb, np, it, smem, full, empty);
       else
-        ok = consume_phase2_multi(jb, np, it, smem, full, empty, red,
-                                  reinterpret_cast<float *>(red + kCWarps * 64 * kRB));
+        ok = consume_phase2_multi(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
     } else if constexpr (PH == 0) {
       ok = consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
     } else if constexpr (FMT == FMT_AFL32) {
+      ok = consume_phase2_reg(jb.L, np, it, smem, full, empty, red, jb.y, parity);
+    } else if constexpr (FMT == FMT_AFL64) {
       ok = consume_phase2<FMT>(jb.L, np, it, smem, full, empty, red, tiles, jb.y, parity);
     } else {
       ok = consume_phase2_rows<FMT>(jb.L, np, it, smem, full, empty, red, jb.y, parity);
@@ -968,12 +1128,24 @@ __global__ void k_decode_slices(const uint8_t *base, const uint64_t *src, const 
     const uint32_t u = unit[s];
     const int e = ue[u], m = um[u];
     const int w = raw ? 64 : 1 + e + m;
-    const uint64_t b0 = src[s];
-    for (uint32_t v = threadIdx.x; v < nv[s]; v += blockDim.x) {
-      const uint64_t bit = b0 + uint64_t(v) * uint64_t(w);
+    const uint64_t s0 = src[s];
+    const bool strided = (s0 & kStridedSlice) != 0;  // a lane column: word k at 32 k
+    const uint64_t b0 = s0 & (kStridedSlice - 1);
+    const uint32_t cnt = nv[s] & 0xffffffu, step = max(1u, nv[s] >> 24);  // values, their stride in the unit
+    for (uint32_t v = threadIdx.x; v < cnt; v += blockDim.x) {
       if (raw) {
+        const uint64_t bit = b0 + uint64_t(v) * uint64_t(w);
         out[dst[s] + v] = *reinterpret_cast<const double *>(base + bit / 8);
+      } else if (strided) {
+        const uint32_t *col = reinterpret_cast<const uint32_t *>(base) + (b0 >> 5);
+        const uint64_t bit = uint64_t(v) * uint64_t(w);
+        const uint64_t q = bit >> 5;
+        const uint32_t sh = uint32_t(bit & 31);
+        const uint32_t a = col[32 * q], b = col[32 * q + 32], c = col[32 * q + 64];
+        const uint64_t code = (uint64_t(__funnelshift_r(b, c, sh)) << 32) | __funnelshift_r(a, b, sh);
+        out[dst[s] + uint64_t(v) * step] = decode_code_exact(code, e, m, mmin[u]);
       } else {
+        const uint64_t bit = b0 + uint64_t(v) * uint64_t(w);
         const uint32_t *wp = reinterpret_cast<const uint32_t *>(base) + (bit >> 5);
         const uint32_t sh = uint32_t(bit & 31);
         const uint64_t code = (uint64_t(__funnelshift_r(wp[1], wp[2], sh)) << 32) | __funnelshift_r(wp[0], wp[1], sh);

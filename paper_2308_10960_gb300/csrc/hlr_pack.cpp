@@ -49,6 +49,29 @@ void copy_bits(const uint8_t *srcb, uint64_t so, uint32_t *dst, uint64_t dof, ui
   }
 }
 
+// Codes of values v0, v0 + step, v0 + 2 step, ... (count values of w bits) of a canonical
+// stream, packed back to back from bit 0 of dst (zeroed; src readable 8 bytes past the end).
+void gather_codes(const uint8_t *src, uint64_t v0, uint64_t step, uint64_t count, int w, uint32_t *dst) {
+  if (w > 56) {
+    for (uint64_t i = 0; i < count; ++i) copy_bits(src, (v0 + i * step) * uint64_t(w), dst, i * uint64_t(w), uint64_t(w));
+    return;
+  }
+  const uint64_t mask = (uint64_t(1) << w) - 1;
+  for (uint64_t i = 0; i < count; ++i) {
+    const uint64_t sb = (v0 + i * step) * uint64_t(w);
+    uint64_t v;
+    std::memcpy(&v, src + (sb >> 3), 8);
+    const uint64_t code = (v >> (sb & 7)) & mask;
+    const uint64_t db = i * uint64_t(w);
+    const uint64_t q = db >> 5;
+    const unsigned sh = unsigned(db & 31);
+    const uint64_t part = code << sh;  // sh + w <= 31 + 56 < 96: at most three words
+    dst[q] |= uint32_t(part);
+    if (sh + unsigned(w) > 32) dst[q + 1] |= uint32_t(part >> 32);
+    if (sh + unsigned(w) > 64) dst[q + 2] |= uint32_t(code >> (64 - sh));
+  }
+}
+
 struct LR {  // host view of a lowrank block with rank > 0
   uint32_t tbase, part0, cbase;
   uint16_t k, nchunks;
@@ -294,6 +317,279 @@ class Builder {
   std::vector<uint32_t> ps_n_, ps_unit_;
 };
 
+// Pieces in the bank-column layout (hlr_internal.h, LaneHdr): the same tasks, segments and aux
+// copies as Builder, but every slice becomes one lane column of a warp region.
+class BcBuilder {
+ public:
+  BcBuilder(const PackInput &in, const std::vector<int64_t> &uvoff, Frag &f, bool want_map, int aux_max)
+      : in_(in), uvoff_(uvoff), f_(f), map_(want_map), aux_max_(aux_max) {}
+
+  void begin_leaf(int64_t nr, int64_t row0) {
+    leaf_nr_ = uint16_t(nr);
+    leaf_row0_ = uint32_t(row0);
+    leaf_start_ = true;
+  }
+  void end_leaf() { flush(PF_END_LEAF); }
+
+  // phase 2, dense block b: the leaf's nr rows (from rowoff) of every column, one lane each
+  void dense(int64_t b, int64_t nr, int64_t rowoff) {
+    const hlr_block_desc &B = in_.blocks[b];
+    const int64_t u = in_.blk_unit0[b];
+    int64_t j0 = 0;
+    while (j0 < B.ncols) {
+      const size_t l0 = lanes_.size();
+      Seg s{};
+      s.kind = SEG_DENSE;
+      s.nr = uint16_t(nr);
+      s.m_min = in_.prm[u].m_min;
+      s.gx = uint32_t(B.col0 + j0);
+      segs_.push_back(s);
+      int64_t fit = 0;
+      for (;;) {
+        const int64_t c = fit + 1;
+        if (j0 + c > B.ncols || c > kMaxCols) break;
+        lanes_.push_back(lane(u, uint64_t(j0 + fit) * B.nrows + rowoff, nr, uint16_t(segs_.size() - 1), uint8_t(fit), 1, 0));
+        if (!fits(aux_elems_ + aligned_span(B.col0 + j0, c))) {
+          lanes_.pop_back();
+          break;
+        }
+        fit = c;
+      }
+      if (fit == 0) {
+        segs_.pop_back();
+        if (l0 == 0) return;  // cannot happen: one column always fits an empty piece
+        flush(0);
+        continue;
+      }
+      Seg &sg = segs_.back();
+      sg.nc = uint16_t(fit);
+      sg.xs = add_aux(0, B.col0 + j0, fit);
+      j0 += fit;
+      if (j0 < B.ncols) flush(0);
+    }
+  }
+
+  // column slices of units u0 + i (i < k), rows [rowoff, rowoff + nr) of each (see Builder)
+  void slices(uint8_t kind, int64_t u0, const LR &L, int64_t nr, int64_t rowoff, int64_t xoff, uint16_t chunk) {
+    const int k = L.k;
+    int lg = 0;
+    if (kind == SEG_X)
+      while ((kSubRows << lg) < nr) ++lg;
+    const int G = 1 << lg;
+    int i0 = 0;
+    while (i0 < k) {
+      Seg s{};
+      s.kind = kind;
+      s.lg = uint8_t(lg);
+      s.nr = uint16_t(nr);
+      if (kind == SEG_X) {
+        s.tidx = L.tbase + uint32_t(i0);
+        s.gx = uint32_t(xoff);
+        s.x.pbase = L.part0 + uint32_t(i0) * L.nchunks;
+        s.x.chunk = chunk;
+        s.x.nchunks = L.nchunks;
+      } else {
+        s.gx = L.tbase + uint32_t(i0);
+      }
+      segs_.push_back(s);
+      const uint16_t si = uint16_t(segs_.size() - 1);
+      int fit = 0;
+      for (;;) {
+        const int c = fit + 1;
+        if (i0 + c > k || c * G > kMaxCols) break;
+        const int64_t u = u0 + i0 + fit;
+        for (int g = 0; g < G; ++g) {
+          // X: lane g of the G lanes of a column takes rows g, g + G, g + 2G, ... of its nr rows,
+          // so that at every step the group's lanes read consecutive x rows (distinct banks)
+          const int64_t nv = kind == SEG_X ? (nr - g + G - 1) / G : nr;
+          lanes_.push_back(lane(u, uint64_t(rowoff + (kind == SEG_X ? g : 0)), nv, si, uint8_t(fit), uint8_t(G),
+                                uint8_t(g), kind == SEG_X ? uint32_t(G) : 1u));
+        }
+        int64_t need = aux_elems_;
+        if (kind == SEG_X)
+          need += aligned_span(xoff, nr) + aligned_span(L.tbase + i0, c);
+        else
+          need += aligned_span(L.tbase + i0, c);
+        if (!fits(need)) {
+          lanes_.resize(lanes_.size() - G);
+          break;
+        }
+        fit = c;
+      }
+      if (fit == 0) {
+        segs_.pop_back();
+        flush(0);
+        continue;
+      }
+      Seg &sg = segs_.back();
+      sg.nc = uint16_t(fit);
+      if (kind == SEG_X) {
+        sg.xs = add_aux(0, xoff, nr);
+        sg.fs = add_aux(2, L.tbase + i0, fit);
+      } else {
+        sg.xs = add_aux(1, L.tbase + i0, fit);
+      }
+      i0 += fit;
+      if (i0 < k) flush(0);
+    }
+  }
+
+  void flush(uint8_t end_flags) {
+    if (segs_.empty()) return;
+    Layout lay;
+    layout(lanes_, &lay);
+    const size_t nseg = segs_.size();
+    const uint32_t nl = uint32_t(lay.nl);
+    const uint32_t hdr_bytes = uint32_t(16 + 32 * nseg + a16(4 * nl));
+    const uint32_t data_w0 = hdr_bytes / 4;
+    PieceHdr ph{};
+    ph.nseg = uint16_t(nseg);
+    ph.ncols = uint16_t(nl);
+    ph.nr = leaf_nr_;
+    ph.flags = uint8_t((leaf_start_ ? PF_START_LEAF : 0) | end_flags);
+    ph.row0 = leaf_row0_;
+    for (int w = 0; w < 4; ++w) ph.h[w] = uint8_t(lay.h[w]);
+    leaf_start_ = false;
+    const size_t total = a16(hdr_bytes + 4 * lay.data_words);
+    const size_t start = f_.bytes.size();
+    f_.piece_off.push_back(start);
+    f_.aux_idx.push_back(uint32_t(f_.aux.size()));
+    f_.bytes.resize(start + total, 0);
+    uint8_t *p = f_.bytes.data() + start;
+    std::memcpy(p, &ph, 16);
+    std::memcpy(p + 16, segs_.data(), 32 * nseg);
+    std::vector<LaneHdr> lh(nl, LaneHdr{0xff, 0, 0, 0});
+    uint32_t *data = reinterpret_cast<uint32_t *>(p + hdr_bytes);
+    uint32_t region[4] = {0, 0, 0, 0};
+    for (int w = 1; w < 4; ++w) region[w] = region[w - 1] + 32 * lay.h[w - 1];
+    std::vector<uint32_t> tmp;
+    for (size_t i = 0; i < lanes_.size(); ++i) {
+      const Lane &L = lanes_[i];
+      const int pos = lay.pos[i];
+      lh[pos] = LaneHdr{uint8_t(L.seg), L.j, L.e, L.m};
+      const uint32_t col = region[pos >> 5] + uint32_t(pos & 31);
+      const uint64_t bits = uint64_t(L.nv) * L.w;
+      tmp.assign(L.words + 3, 0);
+      if (L.step == 1)
+        copy_bits(in_.canon + in_.uoff[L.u], L.v0 * L.w, tmp.data(), 0, bits);
+      else
+        gather_codes(in_.canon + in_.uoff[L.u], L.v0, L.step, L.nv, L.w, tmp.data());
+      for (uint32_t k = 0; k < L.words; ++k) data[col + 32 * k] = tmp[k];
+      if (map_ && L.nv > 0) {
+        f_.s_src.push_back((8 * start + 32 * uint64_t(data_w0 + col)) | kStridedSlice);
+        f_.s_dst.push_back(uint64_t(uvoff_[L.u]) + L.v0);
+        f_.s_n.push_back(L.nv | (L.step << 24));  // values | value stride in the unit << 24
+        f_.s_unit.push_back(uint32_t(L.u));
+      }
+    }
+    std::memcpy(p + 16 + 32 * nseg, lh.data(), 4 * nl);
+    for (auto &a : auxs_) f_.aux.push_back(a);
+    segs_.clear();
+    lanes_.clear();
+    auxs_.clear();
+    aux_elems_ = 0;
+  }
+
+ private:
+  struct Lane {
+    int64_t u;
+    uint64_t v0;      // first value within the unit
+    uint32_t step;    // distance of consecutive values of the slice within the unit
+    uint32_t nv;      // values
+    uint32_t words;   // ceil(nv w / 32)
+    uint16_t seg;
+    uint8_t j, e, m, w, G, sub;
+  };
+  struct Layout {
+    std::vector<int> pos;   // position (lane index in the piece) of every lane
+    int nl = 0;
+    uint32_t h[4] = {0, 0, 0, 0};
+    size_t data_words = 0;
+  };
+
+  Lane lane(int64_t u, uint64_t v0, int64_t nv, uint16_t seg, uint8_t j, uint8_t G, uint8_t sub,
+            uint32_t step = 1) const {
+    Lane L{};
+    L.u = u;
+    L.v0 = v0;
+    L.step = step;
+    L.nv = uint32_t(nv);
+    L.e = uint8_t(in_.prm[u].e);
+    L.m = uint8_t(in_.prm[u].m);
+    L.w = uint8_t(in_.prm[u].w);
+    L.words = words_of(uint64_t(nv) * L.w);
+    L.seg = seg;
+    L.j = j;
+    L.G = G;
+    L.sub = sub;
+    return L;
+  }
+
+  // Groups (the G lanes of one X column, or single lanes) by decreasing G, then decreasing
+  // length; positions are consecutive, so every group stays aligned to its size.
+  static void layout(const std::vector<Lane> &lanes, Layout *out) {
+    std::vector<int> gs;
+    for (size_t i = 0; i < lanes.size(); ++i)
+      if (lanes[i].sub == 0) gs.push_back(int(i));
+    std::stable_sort(gs.begin(), gs.end(), [&](int a, int b) {
+      if (lanes[a].G != lanes[b].G) return lanes[a].G > lanes[b].G;
+      return lanes[a].words > lanes[b].words;
+    });
+    out->pos.assign(lanes.size(), 0);
+    int p = 0;
+    for (int g : gs) {
+      const int G = lanes[g].G;
+      p = (p + G - 1) / G * G;
+      for (int s = 0; s < G; ++s) out->pos[g + s] = p + s;
+      p += G;
+    }
+    out->nl = p;
+    for (int w = 0; w < 4; ++w) out->h[w] = 0;
+    for (size_t i = 0; i < lanes.size(); ++i) {
+      const int w = out->pos[i] >> 5;
+      if (w < 4) out->h[w] = std::max(out->h[w], lanes[i].words);
+    }
+    out->data_words = 32 * size_t(out->h[0] + out->h[1] + out->h[2] + out->h[3]);
+  }
+
+  bool fits(int64_t aux_need) const {
+    if (aux_need > aux_max_) return false;
+    Layout lay;
+    layout(lanes_, &lay);
+    if (lay.nl > kMaxCols) return false;
+    for (int w = 0; w < 4; ++w)
+      if (lay.h[w] > 255) return false;
+    const size_t bytes = 16 + 32 * segs_.size() + a16(4 * size_t(lay.nl)) + 4 * lay.data_words;
+    return bytes <= size_t(kPieceMax);
+  }
+
+  uint16_t add_aux(int which, int64_t start, int64_t cnt) {
+    const int64_t a0 = start & ~int64_t(3);
+    AuxCopy a{};
+    a.elem0 = uint32_t(a0);
+    a.nelem = uint16_t(aligned_span(start, cnt));
+    a.which = uint8_t(which);
+    a.soff = aux_elems_;
+    auxs_.push_back(a);
+    const uint16_t xs = uint16_t(aux_elems_ + (start - a0));
+    aux_elems_ += a.nelem;
+    return xs;
+  }
+
+  const PackInput &in_;
+  const std::vector<int64_t> &uvoff_;
+  Frag &f_;
+  bool map_;
+  int aux_max_;
+  uint16_t leaf_nr_ = 0;
+  uint32_t leaf_row0_ = 0;
+  bool leaf_start_ = false;
+  std::vector<Seg> segs_;
+  std::vector<Lane> lanes_;
+  std::vector<AuxCopy> auxs_;
+  uint32_t aux_elems_ = 0;
+};
+
 // Longest task first onto the least loaded CTA; returns each CTA's tasks in assignment order.
 std::vector<std::vector<int64_t>> assign(const std::vector<Task> &tasks, int nct) {
   std::vector<int64_t> ord(tasks.size());
@@ -432,15 +728,23 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
     std::vector<Frag> frags(nct);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < nct; ++q) {
-      Builder bld(in, uvoff, frags[q], want_map, kAuxMax1);
-      for (int64_t t : per[q]) {
-        const Task &T = items[t];
-        const int64_t b = T.a;
-        const hlr_block_desc &B = in.blocks[b];
-        const int64_t row0 = T.b * kRowsPerItem;
-        bld.slices(SEG_X, in.blk_unit0[b] + B.rank, lr[b], T.c, row0, B.col0 + row0, uint16_t(T.b));
+      auto run = [&](auto &bld) {
+        for (int64_t t : per[q]) {
+          const Task &T = items[t];
+          const int64_t b = T.a;
+          const hlr_block_desc &B = in.blocks[b];
+          const int64_t row0 = T.b * kRowsPerItem;
+          bld.slices(SEG_X, in.blk_unit0[b] + B.rank, lr[b], T.c, row0, B.col0 + row0, uint16_t(T.b));
+        }
+        bld.flush(0);
+      };
+      if (in.raw) {
+        Builder bld(in, uvoff, frags[q], want_map, kAuxMax1);
+        run(bld);
+      } else {
+        BcBuilder bld(in, uvoff, frags[q], want_map, kAuxMax1);
+        run(bld);
       }
-      bld.flush(0);
     }
     concat(frags, out->ph[0], false, out);
   }
@@ -451,21 +755,29 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
     std::vector<Frag> frags(nct);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < nct; ++q) {
-      Builder bld(in, uvoff, frags[q], want_map, kAuxMax2);
-      for (int64_t t : per[q]) {
-        const Task &T = leaves[t];
-        std::vector<int64_t> bl = cover[T.a];
-        std::sort(bl.begin(), bl.end());
-        bld.begin_leaf(T.c, T.b);
-        for (int64_t b : bl) {
-          const hlr_block_desc &B = in.blocks[b];
-          const int64_t rowoff = T.b - B.row0;
-          if (B.kind == HLR_DENSE)
-            bld.dense(b, T.c, rowoff);
-          else if (has_lr[b])
-            bld.slices(SEG_W, in.blk_unit0[b], lr[b], T.c, rowoff, 0, 0);
+      auto run = [&](auto &bld) {
+        for (int64_t t : per[q]) {
+          const Task &T = leaves[t];
+          std::vector<int64_t> bl = cover[T.a];
+          std::sort(bl.begin(), bl.end());
+          bld.begin_leaf(T.c, T.b);
+          for (int64_t b : bl) {
+            const hlr_block_desc &B = in.blocks[b];
+            const int64_t rowoff = T.b - B.row0;
+            if (B.kind == HLR_DENSE)
+              bld.dense(b, T.c, rowoff);
+            else if (has_lr[b])
+              bld.slices(SEG_W, in.blk_unit0[b], lr[b], T.c, rowoff, 0, 0);
+          }
+          bld.end_leaf();
         }
-        bld.end_leaf();
+      };
+      if (in.raw) {
+        Builder bld(in, uvoff, frags[q], want_map, kAuxMax2);
+        run(bld);
+      } else {
+        BcBuilder bld(in, uvoff, frags[q], want_map, kAuxMax2);
+        run(bld);
       }
     }
     concat(frags, out->ph[1], true, out);

@@ -240,9 +240,9 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   H->format = d->format;
   size_t off = 0;
   const size_t o_ph0 = off;
-  off = align_up(off + po.ph[0].bytes.size() + 64, 256);
+  off = align_up(off + po.ph[0].bytes.size() + 512, 256);  // lane-column reads run up to 252 B past a piece
   const size_t o_ph1 = off;
-  off = align_up(off + po.ph[1].bytes.size() + 64, 256);
+  off = align_up(off + po.ph[1].bytes.size() + 512, 256);
   // issue streams: per piece one descriptor, then its aux copies (offsets filled in below)
   std::vector<IssueEnt> ent[2];
   std::vector<uint32_t> cta_e0[2], cta_np[2];
@@ -383,8 +383,10 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     H->slice_unit = std::move(po.slice_unit);
     for (size_t i = 0; i < H->slice_src.size(); ++i) {
       const uint64_t v = H->slice_src[i];
-      const uint64_t ph = v >> 63;  // phase tag
-      H->slice_src[i] = (v & ~(uint64_t(1) << 63)) + 8 * uint64_t(ph ? o_ph1 : o_ph0);
+      const uint64_t ph = v >> 63;                   // phase tag
+      const uint64_t strided = v & kStridedSlice;    // lane-column slice (bank-column piece)
+      const uint64_t addr = v & (kStridedSlice - 1);
+      H->slice_src[i] = (addr + 8 * uint64_t(ph ? o_ph1 : o_ph0)) | strided;
     }
     H->unit_mmin.resize(nunits);
     H->unit_e.resize(nunits);
