@@ -556,13 +556,19 @@ __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     if (16 * k >= nr) break;
+    if (!GEN && 16 * k + 16 <= nr) {  // a whole chunk of the leaf: no row checks
+      uint32_t bit = uint32_t(16 * k) * c.w;
 #pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-      const int r = 16 * k + rr;
-      const bool ok = r < nr;
-      const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
-      const float p = GEN ? float(dec_f64(bc_code64(col, bit), c)) * mult : dec_mul_f32(bc_code32(col, bit), c, mult);
-      if (ok) acc[r] += p;
+      for (int rr = 0; rr < 16; ++rr, bit += c.w) acc[16 * k + rr] += dec_mul_f32(bc_code32(col, bit), c, mult);
+    } else {
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const int r = 16 * k + rr;
+        const bool ok = r < nr;
+        const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
+        const float p = GEN ? float(dec_f64(bc_code64(col, bit), c)) * mult : dec_mul_f32(bc_code32(col, bit), c, mult);
+        if (ok) acc[r] += p;
+      }
     }
   }
 }
