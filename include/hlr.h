@@ -84,8 +84,17 @@ typedef struct {
   const hlr_block_desc *blocks;
   double eps;
   int32_t format;   /* HLR_FMT_AFL_APLR or HLR_FMT_FP64 */
-  int32_t reserved; /* must be 0 */
+  int32_t tuning;   /* 0: default work layout; else HLR_TUNING(sub, leaf, piece_kb), AFL only */
 } hlr_hmatrix_desc;
+
+/* Work layout of the AFL product kernels (chosen per matrix, e.g. by an autotuner; the stored
+ * codes and the result up to FP32 rounding order do not depend on it):
+ *  sub      rows of an X column one lane decodes in phase 1: 32, 64 (default) or 128
+ *           (a column of an item of nr rows is read by the smallest power of two of lanes
+ *           with lanes * sub >= nr);
+ *  leaf     rows of a phase-2 task: 32 or 64 (default; longer leaves are split);
+ *  piece_kb bytes of a piece, in KiB: 4 .. 16 (default 16). */
+#define HLR_TUNING(sub_log2, leaf_log2, piece_kb) ((sub_log2) | ((leaf_log2) << 4) | ((piece_kb) << 8))
 
 /* Sizes of an uploaded matrix (hlr_get_info). Byte counts exclude alignment padding. */
 typedef struct {

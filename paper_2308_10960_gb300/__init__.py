@@ -20,7 +20,7 @@ from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ERR_INVALID, H
 __all__ = [
     "HlrError", "DeviceHMatrix", "HostHMatrix", "upload", "build_kernel_hmatrix", "afl_encode",
     "afl_decode_device", "matvec_batched", "HLR_ACC_FP32", "HLR_ACC_FP64", "HLR_FMT_AFL_APLR", "HLR_FMT_FP64",
-    "HLR_DENSE", "HLR_LOWRANK", "lib_path",
+    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code",
 ]
 
 _ACC = {"fp32": HLR_ACC_FP32, "fp64": HLR_ACC_FP64, HLR_ACC_FP32: HLR_ACC_FP32, HLR_ACC_FP64: HLR_ACC_FP64}
@@ -98,7 +98,7 @@ class _DescBuilder:
         self.desc.blocks = C.cast(arr, C.POINTER(B.BlockDesc))
         self.desc.eps = float(eps)
         self.desc.format = fmt
-        self.desc.reserved = 0
+        self.desc.tuning = 0
 
 
 class DeviceHMatrix:
@@ -175,10 +175,21 @@ class DeviceHMatrix:
             pass
 
 
-def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None) -> DeviceHMatrix:
+def tuning_code(sub_rows: int = 64, leaf_rows: int = 64, piece_kb: int = 16) -> int:
+    """HLR_TUNING of include/hlr.h: rows per lane of an X column (32/64/128), rows of a
+    phase-2 task (32/64), piece size in KiB (4..16); the defaults give 0."""
+    if (sub_rows, leaf_rows, piece_kb) == (64, 64, 16):
+        return 0
+    if sub_rows not in (32, 64, 128) or leaf_rows not in (32, 64) or not 4 <= piece_kb <= 16:
+        raise HlrError(HLR_ERR_INVALID, "bad tuning")
+    return (sub_rows.bit_length() - 1) | ((leaf_rows.bit_length() - 1) << 4) | (piece_kb << 8)
+
+
+def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None, tuning: int = 0) -> DeviceHMatrix:
     """Upload an H-matrix given as a list of block dicts (row0, nrows, col0, ncols, kind and D
     or W, S, X as numpy arrays, cluster order) with perm[p] = original index of position p."""
     db = _DescBuilder(n, perm, blocks, eps, _FMT[fmt])
+    db.desc.tuning = int(tuning)
     h = C.c_uint64(0)
     nbytes = C.c_size_t(0)
     B.check(B.lib.hlr_upload(C.byref(db.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))
@@ -246,10 +257,12 @@ class HostHMatrix:
                 if k else np.zeros((d.ncols, 0))
         return b
 
-    def upload(self, fmt="afl", eps: float | None = None, stream=None) -> DeviceHMatrix:
-        """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU."""
+    def upload(self, fmt="afl", eps: float | None = None, stream=None, tuning: int = 0) -> DeviceHMatrix:
+        """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU. tuning:
+        work layout of the AFL kernels (``tuning_code``; 0 = default)."""
         self.desc.format = _FMT[fmt]
         self.desc.eps = self.eps if eps is None else float(eps)
+        self.desc.tuning = int(tuning)
         h = C.c_uint64(0)
         nbytes = C.c_size_t(0)
         B.check(B.lib.hlr_upload(C.byref(self.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))

@@ -51,7 +51,7 @@ class BlockDesc(C.Structure):
 
 class HMatrixDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("perm", _i64p), ("nblocks", C.c_int64), ("blocks", C.POINTER(BlockDesc)),
-                ("eps", C.c_double), ("format", C.c_int32), ("reserved", C.c_int32)]
+                ("eps", C.c_double), ("format", C.c_int32), ("tuning", C.c_int32)]
 
 
 class Info(C.Structure):

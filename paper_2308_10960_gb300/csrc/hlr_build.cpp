@@ -506,7 +506,7 @@ extern "C" int hlr_host_describe(const hlr_host_hmatrix *hm, hlr_hmatrix_desc *d
   d->blocks = hm->descs.data();
   d->eps = hm->eps;
   d->format = HLR_FMT_AFL_APLR;
-  d->reserved = 0;
+  d->tuning = 0;
   return HLR_OK;
 }
 

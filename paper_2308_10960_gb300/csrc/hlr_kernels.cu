@@ -474,7 +474,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
     }
     // the G lanes of a column (an aligned group) sum their row parts in a fixed order
 #pragma unroll
-    for (uint32_t o = 1; o < 4; o <<= 1) {
+    for (uint32_t o = 1; o < 32; o <<= 1) {
       const A v = __shfl_xor_sync(kFull, dot, o);
       if (o < G) dot += v;
     }
@@ -906,7 +906,7 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
     }
     // the G lanes of a column (an aligned group) sum their row parts in a fixed order
 #pragma unroll
-    for (uint32_t o = 1; o < 4; o <<= 1) {
+    for (uint32_t o = 1; o < 32; o <<= 1) {
 #pragma unroll
       for (int q = 0; q < kRB; ++q) {
         const float v = __shfl_xor_sync(kFull, acc[q], o);

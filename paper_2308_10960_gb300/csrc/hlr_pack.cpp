@@ -13,6 +13,7 @@
 #include <omp.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <numeric>
 #include <queue>
@@ -357,7 +358,10 @@ class BcBuilder {
       }
       if (fit == 0) {
         segs_.pop_back();
-        if (l0 == 0) return;  // cannot happen: one column always fits an empty piece
+        if (segs_.empty()) {  // not even one column fits an empty piece
+          failed = true;
+          return;
+        }
         flush(0);
         continue;
       }
@@ -373,8 +377,13 @@ class BcBuilder {
   void slices(uint8_t kind, int64_t u0, const LR &L, int64_t nr, int64_t rowoff, int64_t xoff, uint16_t chunk) {
     const int k = L.k;
     int lg = 0;
-    if (kind == SEG_X)
-      while ((kSubRows << lg) < nr) ++lg;
+    if (kind == SEG_X) {
+      int wmax = 1;
+      for (int i = 0; i < k; ++i) wmax = std::max(wmax, int(in_.prm[u0 + i].w));
+      // a lane column must leave room in a piece: one warp region of 32 such columns
+      const int64_t max_words = std::max<int64_t>(8, (in_.piece_max - 1024) / 128);
+      while ((in_.sub_rows << lg) < nr || int64_t((nr + (1 << lg) - 1) >> lg) * wmax > max_words * 32) ++lg;
+    }
     const int G = 1 << lg;
     int i0 = 0;
     while (i0 < k) {
@@ -418,6 +427,10 @@ class BcBuilder {
       }
       if (fit == 0) {
         segs_.pop_back();
+        if (segs_.empty()) {
+          failed = true;
+          return;
+        }
         flush(0);
         continue;
       }
@@ -560,7 +573,7 @@ class BcBuilder {
     for (int w = 0; w < 4; ++w)
       if (lay.h[w] > 255) return false;
     const size_t bytes = 16 + 32 * segs_.size() + a16(4 * size_t(lay.nl)) + 4 * lay.data_words;
-    return bytes <= size_t(kPieceMax);
+    return bytes <= size_t(in_.piece_max);
   }
 
   uint16_t add_aux(int which, int64_t start, int64_t cnt) {
@@ -576,6 +589,10 @@ class BcBuilder {
     return xs;
   }
 
+ public:
+  bool failed = false;  // a column did not fit an empty piece
+
+ private:
   const PackInput &in_;
   const std::vector<int64_t> &uvoff_;
   Frag &f_;
@@ -699,8 +716,8 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
   const auto &cover = *in.cover;
   const auto &brk = *in.brk;
   for (size_t iv = 0; iv < cover.size(); ++iv) {
-    for (int64_t r0 = brk[iv]; r0 < brk[iv + 1]; r0 += kLeafRows) {
-      const int64_t nr = std::min<int64_t>(kLeafRows, brk[iv + 1] - r0);
+    for (int64_t r0 = brk[iv]; r0 < brk[iv + 1]; r0 += in.leaf_rows) {
+      const int64_t nr = std::min<int64_t>(in.leaf_rows, brk[iv + 1] - r0);
       double cost = 64;
       int nc = 0;
       for (int64_t b : cover[iv]) {
@@ -720,6 +737,7 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
   }
   out->nitems = int64_t(items.size());
   out->nleaves = int64_t(leaves.size());
+  std::atomic<int> failed{0};
 
   // ---- phase 1 (items)
   {
@@ -744,6 +762,7 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
       } else {
         BcBuilder bld(in, uvoff, frags[q], want_map, kAuxMax1);
         run(bld);
+        if (bld.failed) failed.store(1);
       }
     }
     concat(frags, out->ph[0], false, out);
@@ -778,10 +797,12 @@ int pack_work(const PackInput &in, const int nct2[2], bool want_map, PackOutput 
       } else {
         BcBuilder bld(in, uvoff, frags[q], want_map, kAuxMax2);
         run(bld);
+        if (bld.failed) failed.store(1);
       }
     }
     concat(frags, out->ph[1], true, out);
   }
+  if (failed) return set_error(HLR_ERR_UNSUPPORTED, "hlr_upload: a column does not fit one piece of this work layout");
   return HLR_OK;
 }
 

@@ -19,6 +19,9 @@ struct PackInput {
   const uint8_t *canon = nullptr;          // canonical streams (64 bytes readable past the end)
   const std::vector<std::vector<int64_t>> *cover = nullptr;  // blocks covering each row interval
   const std::vector<int64_t> *brk = nullptr;                 // row interval breakpoints
+  int sub_rows = kSubRows;      // AFL phase 1: rows of an X column per lane
+  int leaf_rows = kLeafRows;    // phase-2 task rows
+  int piece_max = kPieceMax;    // AFL piece bytes
 };
 
 struct PhaseOut {

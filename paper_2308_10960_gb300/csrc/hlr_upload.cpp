@@ -74,7 +74,16 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   if (d->nblocks <= 0 || !d->blocks) return set_error(HLR_ERR_INVALID, "hlr_upload: no blocks");
   if (d->format != HLR_FMT_AFL_APLR && d->format != HLR_FMT_FP64)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
-  if (d->reserved != 0) return set_error(HLR_ERR_INVALID, "hlr_upload: reserved must be 0");
+  int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
+  if (d->tuning != 0) {
+    const int sl = d->tuning & 15, ll = (d->tuning >> 4) & 15, kb = (d->tuning >> 8) & 255;
+    if (d->format != HLR_FMT_AFL_APLR || sl < 5 || sl > 7 || ll < 5 || ll > 6 || kb < 4 || kb > kPieceMax / 1024 ||
+        (d->tuning >> 16) != 0)
+      return set_error(HLR_ERR_INVALID, "hlr_upload: bad tuning (see HLR_TUNING; AFL format only)");
+    sub_rows = 1 << sl;
+    leaf_rows = 1 << ll;
+    piece_max = kb * 1024;
+  }
   if (d->format == HLR_FMT_AFL_APLR && !(d->eps > 0.0 && d->eps < 1.0))
     return set_error(HLR_ERR_INVALID, "hlr_upload: eps must be in (0, 1)");
   const bool afl = d->format == HLR_FMT_AFL_APLR;
@@ -225,6 +234,9 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   // ---- work lists
   in.cover = &cover;
   in.brk = &brk;
+  in.sub_rows = sub_rows;
+  in.leaf_rows = leaf_rows;
+  in.piece_max = piece_max;
   int dev = 0;
   cudaGetDevice(&dev);
   int nct[2] = {0, 0};

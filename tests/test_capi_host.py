@@ -3,6 +3,7 @@ symbol include/hlr.h declares; the host AFL encoder is byte-exact with the oracl
 native construction reproduces the oracle's cluster tree, block tree and ranks and meets Eq. 1;
 upload rejects invalid descriptors before touching the GPU."""
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -131,3 +132,32 @@ def test_host_errors_have_messages():
     assert "non-finite" in str(ei.value)
     with pytest.raises(hg.HlrError):
         hg.build_kernel_hmatrix(np.zeros((4, 2)), "exp2d", 0.0, scale=1.0)
+
+
+def test_tuning_codes_and_rejection():
+    """HLR_TUNING of the header and its Python mirror agree; bad layouts are refused before any
+    device work."""
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hlr.h")).read()
+    assert "#define HLR_TUNING(sub_log2, leaf_log2, piece_kb) ((sub_log2) | ((leaf_log2) << 4) | ((piece_kb) << 8))" in hdr
+    assert hg.tuning_code() == 0
+    assert hg.tuning_code(32, 64, 16) == 5 | (6 << 4) | (16 << 8)
+    assert hg.tuning_code(128, 32, 8) == 7 | (5 << 4) | (8 << 8)
+    with pytest.raises(hg.HlrError):
+        hg.tuning_code(16, 64, 16)
+    bl = _tiny_blocks()
+    for bad in [3 | (6 << 4) | (16 << 8), 6 | (7 << 4) | (16 << 8), 6 | (6 << 4) | (2 << 8), 6 | (6 << 4) | (17 << 8),
+                -1, 1 << 20]:
+        with pytest.raises(hg.HlrError, match="tuning"):
+            hg.upload(5, None, bl, 1e-6, tuning=bad)
+    with pytest.raises(hg.HlrError, match="tuning"):
+        hg.upload(5, None, bl, 1e-6, fmt="fp64", tuning=hg.tuning_code(32, 64, 16))
+
+
+def test_autotuner_rank_classes():
+    from paper_2308_10960_gb300 import tune
+    assert tune.rank_class({"rank_sum": 1000, "nlowrank": 90}, 8) == (8, 8)
+    assert tune.rank_class({"rank_sum": 0, "nlowrank": 0}, 1) == (1, 1)
+    t = tune.Autotuner()
+    assert t.lookup({"rank_sum": 100, "nlowrank": 10}) is None
+    t.table[(8, 1)] = (32, 64, 16)
+    assert t.lookup({"rank_sum": 100, "nlowrank": 10}) == hg.tuning_code(32, 64, 16)
