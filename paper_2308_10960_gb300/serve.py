@@ -251,7 +251,9 @@ class GpuBackend:
         self.host = dict(host_mats)
         self.dev = {}
         self.acc_cg = acc_cg
-        self.stream = torch.cuda.Stream()
+        # product batches on a high-priority stream: their CTAs are scheduled ahead of the
+        # solves' kernels, so a short product does not queue behind long CG runs
+        self.stream = torch.cuda.Stream(priority=-1)
         self._bytes = {}
         self._alg = {}
         self._local = threading.local()
