@@ -43,10 +43,12 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS comparison legs")
-    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve"],
+    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve", "small", "scale"],
                     help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
                          "uneven size with 1/8/32 right-hand sides in one batched launch sequence; serve: "
-                         "Poisson requests (70%% products, 30%% CG solves) against resident Matern matrices")
+                         "Poisson requests (70%% products, 30%% CG solves) against resident Matern matrices; "
+                         "small: n=4096 2D exponential kernel, latency with L2 flushed; scale: n=2^21 sphere, "
+                         "1 and 32 right-hand sides")
     ap.add_argument("--serve-mats", type=int, default=16)
     ap.add_argument("--serve-min-n", type=int, default=16384)
     ap.add_argument("--serve-max-n", type=int, default=262144)
@@ -579,6 +581,113 @@ def run_serve(args, world: int, rank: int, local: int):
     be.close()
 
 
+def run_small(args, world: int, rank: int, local: int):
+    """n = 4096 points uniform in [0,1]^2 (seed 0), exp(-r/0.2) + 1e-2 I, eps from --eps: the
+    whole compressed matrix fits in L2, so L2 is flushed (a 256 MB buffer is written) before
+    every product and each product is timed alone with CUDA events; the median latency is
+    reported (value = algorithmic bytes / median time)."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = synth.exp2d_problem(4096, seed=0)
+    Hh = hg.build_kernel_hmatrix(p.points, "exp2d", args.eps, scale=p.params["scale"], diag=p.params["diag"])
+    A = Hh.upload("afl")
+    info = A.info
+    x = torch.from_numpy(synth.rhs(4096, 1)).to(dev)
+    y = torch.zeros(4096, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        A.matvec(x, y, acc="fp32", stream=stream)
+    times = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0.record(stream)
+        A.matvec(x, y, acc="fp32", stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e3)
+    clk = clocks.stop()
+    A.check()
+    times.sort()
+    med = times[len(times) // 2]
+    if rank == 0:
+        out = {"metric": METRIC, "value": info["algorithmic_bytes"] / (med * 1e-6) / 1e9, "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": med / 1e3,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"exp2d n=4096 eps={args.eps:g} (fits in L2; L2 flushed by a 256 MB write before "
+                                      f"each product, each product timed alone)", "l2": "flushed between products"},
+               "latency_us": {"median": med, "min": times[0], "p90": times[int(0.9 * (len(times) - 1))]},
+               "matrix": {"algorithmic_bytes": info["algorithmic_bytes"], "nblocks": info["nblocks"]},
+               "clocks": clk, "gpu_launches": int(info["launches"]) * args.steps}
+        print(json.dumps(out), flush=True)
+    A.free()
+    Hh.free()
+
+
+def run_scale(args, world: int, rank: int, local: int):
+    """n = 2^21 Fibonacci points on the sphere, 1/(4 pi r) with the mean row sum (1024 sampled
+    rows) on the diagonal, eps from --eps: single-column products and 32-column products
+    (hlr_matvec_batched). The sampled-row check against direct kernel evaluation is
+    tests/test_gpu_scale.py."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 2 ** 21
+    t0 = time.perf_counter()
+    p = synth.laplace_problem(n)
+    Hh = hg.build_kernel_hmatrix(p.points, "laplace", args.eps, diag=p.params["diag"])
+    t_build = time.perf_counter() - t0
+    A = Hh.upload("afl")
+    Hh.free()
+    info = A.info
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(synth.rhs(n, 1)).to(dev)
+    y = torch.zeros(n, dtype=torch.float64, device=dev)
+    for _ in range(max(3, args.warmup)):
+        A.matvec(x, y, acc="fp32", stream=stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    el = time_loop(lambda: A.matvec(x, y, acc="fp32", stream=stream), args.steps, stream)
+    clk = clocks.stop()
+    X = torch.from_numpy(synth.rhs(n * 32, 3)).to(dev).view(32, n)
+    Y = torch.zeros_like(X)
+    for _ in range(2):
+        hg.matvec_batched([A], [X], [Y], acc="fp32", stream=stream)
+    k32 = max(3, args.steps // 20)
+    el32 = time_loop(lambda: hg.matvec_batched([A], [X], [Y], acc="fp32", stream=stream), k32, stream)
+    A.check()
+    bytes1 = float(info["algorithmic_bytes"])
+    b32 = multi_rhs_bytes(info, n, 32)
+    t1 = el / args.steps
+    t32 = el32 / k32
+    peaks = measured_peaks()
+    if rank == 0:
+        out = {"metric": METRIC, "value": bytes1 / t1 / 1e9 * world, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": t1 * 1e3, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"laplace-sphere n=2097152 eps={args.eps:g} AFL-APLR, single and 32 RHS",
+                          "l2": "inputs larger than L2"},
+               "pct_hbm_peak": bytes1 / t1 / 1e9 / peaks["hbm_gbs"],
+               "rhs32": {"ms_per_step": t32 * 1e3, "GB/s": b32 / t32 / 1e9, "algorithmic_bytes": b32,
+                         "speedup_vs_32_single_products": 32 * t1 / t32},
+               "matrix": {"nblocks": info["nblocks"], "rank_sum": info["rank_sum"], "algorithmic_bytes": bytes1,
+                          "fp64_bytes": info["fp64_bytes"], "device_bytes": info["device_bytes"], "build_s": t_build},
+               "clocks": clk, "gpu_launches": int(info["launches"]) * args.steps}
+        print(json.dumps(out), flush=True)
+    A.free()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -598,6 +707,10 @@ def main():
         run_batch(args, world, rank, local)
     elif args.workload == "serve":
         run_serve(args, world, rank, local)
+    elif args.workload == "small":
+        run_small(args, world, rank, local)
+    elif args.workload == "scale":
+        run_scale(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -234,6 +234,22 @@ __device__ __forceinline__ uint64_t bc_code64(const uint32_t *col, uint32_t bit)
   const uint32_t a = col[32 * q], b = col[32 * q + 32], c = col[32 * q + 64];
   return (uint64_t(__funnelshift_r(b, c, bit)) << 32) | __funnelshift_r(a, b, bit);
 }
+// The same with 32-bit shared-memory addresses (col_s: byte address of the column's word 0,
+// x_s: of an FP32 staged multiplier), for the phase-1 inner loop.
+__device__ __forceinline__ uint32_t ld_shared_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float ld_shared_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t bc_code32_s(uint32_t col_s, uint32_t bit) {
+  const uint32_t a = col_s + ((bit >> 5) << 7);
+  return __funnelshift_r(ld_shared_u32(a), ld_shared_u32(a + 128), bit);
+}
 __device__ __forceinline__ const LaneHdr *lane_hdrs(const uint8_t *slot, const PieceHdr *ph) {
   return reinterpret_cast<const LaneHdr *>(slot + 16 + 32 * size_t(ph->nseg));
 }
@@ -456,8 +472,12 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
             uint32_t bit = 0;
             if constexpr (FMT == FMT_AFL32) {
               if (c.fast32) {
+                const uint32_t col_s = smem_u32(col);
+                const uint32_t xstep = uint32_t(xs) * 4u;
+                uint32_t xa = smem_u32(xr);
 #pragma unroll 8
-                for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(dec_f32(bc_code32(col, bit), c), xr[r * xs], dot);
+                for (int r = 0; r < rc; ++r, bit += c.w, xa += xstep)
+                  dot = fmaf(dec_f32(bc_code32_s(col_s, bit), c), ld_shared_f32(xa), dot);
               } else {
                 for (int r = 0; r < rc; ++r, bit += c.w)
                   dot = fmaf(float(dec_f64(bc_code32(col, bit), c)), xr[r * xs], dot);
