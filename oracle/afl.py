@@ -28,6 +28,18 @@ design notes of the repository):
 * decoding: v = bits((field + 1023) << 52 | mant << (52 - m)), a = (v - 1) * m_min in IEEE
   FP64 round-to-nearest (no fused multiply-add), negated when the sign bit is set.
 * APLR: delta = eps * sigma_0 (spectral norm), u~_i = (eps * sigma_0) / sigma_i.
+
+Byte-aligned variants (Section 3.2, after AFL):
+
+* AFLP: AFL with the mantissa width raised to the smallest m' >= m for which 1 + e + m' is a
+  multiple of 8 (e taken after rounding at m', as for AFL); decoded exactly like AFL.
+* BFL: 8 exponent bits, i.e. the FP32 layout: the value is cast to FP32 (round to nearest
+  even), its bit pattern rounded half up to m' mantissa bits, m' the smallest of 7, 15, 23 with
+  m' >= m (23 when m > 23), and the top 1 + 8 + m' bits stored; decoded by shifting the code
+  back into an FP32 pattern.
+* DFL: 11 exponent bits, the FP64 layout: the FP64 pattern rounded half up to m' mantissa
+  bits, m' the smallest of 4, 12, ..., 52 with m' >= m, top 1 + 11 + m' bits stored.
+  BFL and DFL store no m_min (it is 1) and e is the fixed exponent width.
 """
 from __future__ import annotations
 
@@ -58,14 +70,19 @@ def aplr_precisions(sigma: np.ndarray, eps: float) -> np.ndarray:
     return np.array([delta / float(s) for s in sigma], dtype=np.float64)
 
 
+FORMATS = ("afl", "aflp", "bfl", "dfl")
+
+
 @dataclass(frozen=True)
 class AFLUnit:
-    """One AFL-compressed data unit: ``n`` values of width w = 1 + e + m in ``data``."""
+    """One compressed data unit: ``n`` values of width w = 1 + e + m in ``data``, in format
+    ``fmt`` (AFL, or its byte-aligned variants AFLP, BFL, DFL)."""
     n: int
     m_min: float
     e: int
     m: int
     data: bytes
+    fmt: str = "afl"
 
     @property
     def w(self) -> int:
@@ -87,10 +104,14 @@ def _round_to_mantissa(v: np.ndarray, m: int) -> np.ndarray:
 
 def codes_of(a: np.ndarray, u: float) -> tuple[np.ndarray, float, int, int]:
     """Integer codes of the values a (storage order) at precision u: (codes, m_min, e, m)."""
+    return codes_at(a, mantissa_bits(u))
+
+
+def codes_at(a: np.ndarray, m: int) -> tuple[np.ndarray, float, int, int]:
+    """AFL codes of the values a with m mantissa bits: (codes, m_min, e, m)."""
     a = np.ascontiguousarray(a, dtype=np.float64).ravel()
     if not np.all(np.isfinite(a)):
         raise ValueError("AFL input must be finite")
-    m = mantissa_bits(u)
     mag = np.abs(a)
     nonzero = mag != 0.0
     if not np.any(nonzero):
@@ -128,15 +149,82 @@ def unpack(data: bytes, n: int, w: int) -> np.ndarray:
     return (bitmat << np.arange(w, dtype=np.uint64)[None, :]).sum(axis=1, dtype=np.uint64)
 
 
-def encode(a: np.ndarray, u: float) -> AFLUnit:
-    """AFL-encode the values a (in storage order) at precision u."""
+def encode(a: np.ndarray, u: float, fmt: str = "afl") -> AFLUnit:
+    """Encode the values a (in storage order) at precision u in format fmt."""
+    if fmt == "aflp":
+        return encode_aflp(a, u)
+    if fmt == "bfl":
+        return encode_bfl(a, u)
+    if fmt == "dfl":
+        return encode_dfl(a, u)
+    if fmt != "afl":
+        raise ValueError(f"unknown format {fmt!r}")
     code, m_min, e, m = codes_of(a, u)
     return AFLUnit(n=code.size, m_min=m_min, e=e, m=m, data=pack(code, 1 + e + m))
 
 
+def encode_aflp(a: np.ndarray, u: float) -> AFLUnit:
+    """AFLP: AFL with the smallest m' >= m(u) that makes 1 + e + m' a multiple of 8."""
+    m = mantissa_bits(u)
+    while True:
+        code, m_min, e, mm = codes_at(a, m)
+        if (1 + e + m) % 8 == 0 or m == MANT_BITS:
+            break
+        m += 1
+    return AFLUnit(n=code.size, m_min=m_min, e=e, m=m, data=pack(code, 1 + e + m), fmt="aflp")
+
+
+def bfl_mantissa(u: float) -> int:
+    """BFL mantissa width: the smallest of 7, 15, 23 that is >= m(u) (23 if none is)."""
+    m = mantissa_bits(u)
+    return next((mp for mp in (7, 15, 23) if mp >= m), 23)
+
+
+def dfl_mantissa(u: float) -> int:
+    """DFL mantissa width: the smallest of 4, 12, ..., 52 that is >= m(u)."""
+    m = mantissa_bits(u)
+    return next(mp for mp in range(4, 53, 8) if mp >= m)
+
+
+def encode_bfl(a: np.ndarray, u: float) -> AFLUnit:
+    """BFL: FP32 cast, mantissa rounded half up to m' bits, top 9 + m' bits of the pattern."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    mp = bfl_mantissa(u)
+    x = a.astype(np.float32)
+    if not np.all(np.isfinite(x)):
+        raise ValueError("BFL input must be finite in FP32")
+    b = x.view(np.uint32).astype(np.uint64)
+    if mp < 23:
+        b = (b + np.uint64(1 << (22 - mp))) & ~np.uint64((1 << (23 - mp)) - 1)
+    if np.any(((b >> np.uint64(23)) & np.uint64(0xFF)) == np.uint64(0xFF)):
+        raise ValueError("BFL rounding overflows FP32")
+    code = b >> np.uint64(23 - mp)
+    return AFLUnit(n=code.size, m_min=1.0, e=8, m=mp, data=pack(code, 9 + mp), fmt="bfl")
+
+
+def encode_dfl(a: np.ndarray, u: float) -> AFLUnit:
+    """DFL: the FP64 pattern rounded half up to m' mantissa bits, top 12 + m' bits."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    if not np.all(np.isfinite(a)):
+        raise ValueError("DFL input must be finite")
+    mp = dfl_mantissa(u)
+    b = a.view(np.uint64).copy()
+    if mp < MANT_BITS:
+        b = (b + np.uint64(1 << (MANT_BITS - 1 - mp))) & ~np.uint64((1 << (MANT_BITS - mp)) - 1)
+    if np.any(((b >> np.uint64(52)) & np.uint64(0x7FF)) == np.uint64(0x7FF)):
+        raise ValueError("DFL rounding overflows FP64")
+    code = b >> np.uint64(MANT_BITS - mp)
+    return AFLUnit(n=code.size, m_min=1.0, e=11, m=mp, data=pack(code, 12 + mp), fmt="dfl")
+
+
 def decode(unit: AFLUnit) -> np.ndarray:
-    """Decode an AFL unit to FP64: a = (v - 1) * m_min, negated for a set sign bit."""
+    """Decode a unit to FP64. AFL/AFLP: a = (v - 1) * m_min, negated for a set sign bit;
+    BFL: the code shifted back into an FP32 pattern; DFL: into an FP64 pattern."""
     code = unpack(unit.data, unit.n, unit.w)
+    if unit.fmt == "bfl":
+        return (code << np.uint64(23 - unit.m)).astype(np.uint32).view(np.float32).astype(np.float64)
+    if unit.fmt == "dfl":
+        return (code << np.uint64(MANT_BITS - unit.m)).view(np.float64).copy()
     e, m = unit.e, unit.m
     mant = code & np.uint64((1 << m) - 1)
     field = (code >> np.uint64(m)) & np.uint64((1 << e) - 1)

@@ -281,8 +281,10 @@ class CHMatrix:
     eps: float
 
 
-def compress(H: HMatrix, eps: float | None = None, precision_override: float | None = None) -> CHMatrix:
-    """AFL (dense) / AFL-APLR (lowrank) compression of every leaf.
+def compress(H: HMatrix, eps: float | None = None, precision_override: float | None = None,
+             fmt: str = "afl") -> CHMatrix:
+    """AFL (dense) / AFL-APLR (lowrank) compression of every leaf; fmt selects AFL or one of
+    its byte-aligned variants AFLP, BFL, DFL (Section 3.2), with the same precisions.
 
     ``precision_override`` replaces every precision (tests use 2^-60 to make m = 52).
     """
@@ -291,14 +293,14 @@ def compress(H: HMatrix, eps: float | None = None, precision_override: float | N
     for b in H.blocks:
         if b.kind == DENSE:
             u = eps if precision_override is None else precision_override
-            units = [afl.encode(b.D.ravel(order="F"), u)]
+            units = [afl.encode(b.D.ravel(order="F"), u, fmt)]
             out.append(CBlock(b.row0, b.nrows, b.col0, b.ncols, DENSE, None, units))
         else:
             us = afl.aplr_precisions(b.S, eps)
             if precision_override is not None:
                 us = np.full_like(us, precision_override)
-            units = [afl.encode(b.W[:, i], us[i]) for i in range(b.rank)]
-            units += [afl.encode(b.X[:, i], us[i]) for i in range(b.rank)]
+            units = [afl.encode(b.W[:, i], us[i], fmt) for i in range(b.rank)]
+            units += [afl.encode(b.X[:, i], us[i], fmt) for i in range(b.rank)]
             out.append(CBlock(b.row0, b.nrows, b.col0, b.ncols, LOWRANK, b.S.copy(), units))
     return CHMatrix(H.n, H.perm.copy(), out, eps)
 
