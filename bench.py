@@ -387,7 +387,25 @@ def run_ours(args, world: int, rank: int, local: int):
                              "speedup_vs_r_single_products": r * t32 / tm}
             del X, Y
         A.check()
+        formats = {}
+        for fmt in ("aflp", "bfl", "dfl"):
+            Af = Hh.upload(fmt)
+            inf_f = Af.info
+
+            def stepf():
+                Af.matvec(x, y, acc="fp32", stream=stream)
+            for _ in range(3):
+                stepf()
+            kf = max(20, steps_cmp // 4)
+            tf = time_loop(stepf, kf, stream) / kf
+            Af.check()
+            comp = inf_f["stream_bytes"] + inf_f["header_bytes"] + 8 * inf_f["rank_sum"]
+            formats[fmt] = {"ms_per_step": tf * 1e3, "GB/s": inf_f["algorithmic_bytes"] / tf / 1e9,
+                            "compressed_bytes": comp, "ratio": comp / inf_f["fp64_bytes"],
+                            "speedup_vs_afl": t32 / tf}
+            Af.free()
         extra = {
+            "formats": formats,
             "multi_rhs": multi,
             "afl_fp64_acc": {"ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9},
             "plain_fp64": {"ms_per_step": tp * 1e3, "GB/s": infp["algorithmic_bytes"] / tp / 1e9,

@@ -45,6 +45,10 @@ extern "C" {
 
 #define HLR_FMT_AFL_APLR 1  /* dense leaves: one AFL unit at eps; lowrank: AFL-APLR columns  */
 #define HLR_FMT_FP64     2  /* plain uncompressed FP64 factors (the baseline H-matvec)        */
+/* Byte-aligned variants of AFL (Section 3.2), same per-unit precisions as HLR_FMT_AFL_APLR:  */
+#define HLR_FMT_AFLP     3  /* AFL with m raised to the smallest m' making 1 + e + m' a multiple of 8 */
+#define HLR_FMT_BFL      4  /* FP32 layout: FP32 cast, mantissa rounded to m' in {7, 15, 23}      */
+#define HLR_FMT_DFL      5  /* FP64 layout: mantissa rounded to m' in {4, 12, ..., 52}             */
 
 /* ---- product flags ---------------------------------------------------------------------- */
 #define HLR_ACC_FP64 0  /* decode to FP64 and accumulate in FP64 everywhere                    */
@@ -83,7 +87,7 @@ typedef struct {
   int64_t nblocks;
   const hlr_block_desc *blocks;
   double eps;
-  int32_t format;   /* HLR_FMT_AFL_APLR or HLR_FMT_FP64 */
+  int32_t format;   /* HLR_FMT_AFL_APLR, HLR_FMT_AFLP, HLR_FMT_BFL, HLR_FMT_DFL or HLR_FMT_FP64 */
   int32_t tuning;   /* 0: default work layout; else HLR_TUNING(sub, leaf, piece_kb), AFL only */
 } hlr_hmatrix_desc;
 
@@ -194,6 +198,13 @@ int hlr_profile_read(hlr_handle h, double *kernel_ms, int *calls);
  * HLR_ERR_INVALID for NaN/Inf input or u <= 0; HLR_ERR_OOM if cap is too small. */
 int hlr_afl_encode(const double *a, int64_t n, double u, double *m_min, int32_t *e, int32_t *m,
                    uint8_t *out, size_t cap, size_t *nbytes);
+
+/* hlr_afl_encode for any compressed format (HLR_FMT_AFL_APLR, HLR_FMT_AFLP, HLR_FMT_BFL,
+ * HLR_FMT_DFL), Section 3.2: same arguments and errors; for BFL and DFL *m_min is 1 and *e the
+ * fixed exponent width (8, 11). BFL also fails (HLR_ERR_INVALID) for values that are not finite
+ * in FP32 after the cast and rounding. */
+int hlr_encode(int32_t format, const double *a, int64_t n, double u, double *m_min, int32_t *e, int32_t *m,
+               uint8_t *out, size_t cap, size_t *nbytes);
 
 /* Decode one AFL stream on the GPU into n FP64 values, bit-exact IEEE round-to-nearest
  * ((v - 1) * m_min without contraction, Section 3.2). stream_dev must be 16-byte aligned and

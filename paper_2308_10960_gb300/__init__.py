@@ -20,11 +20,13 @@ from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ERR_INVALID, H
 __all__ = [
     "HlrError", "DeviceHMatrix", "HostHMatrix", "upload", "build_kernel_hmatrix", "afl_encode",
     "afl_decode_device", "matvec_batched", "HLR_ACC_FP32", "HLR_ACC_FP64", "HLR_FMT_AFL_APLR", "HLR_FMT_FP64",
-    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code",
+    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code", "encode",
 ]
 
 _ACC = {"fp32": HLR_ACC_FP32, "fp64": HLR_ACC_FP64, HLR_ACC_FP32: HLR_ACC_FP32, HLR_ACC_FP64: HLR_ACC_FP64}
-_FMT = {"afl": HLR_FMT_AFL_APLR, "fp64": HLR_FMT_FP64, HLR_FMT_AFL_APLR: HLR_FMT_AFL_APLR, HLR_FMT_FP64: HLR_FMT_FP64}
+_FMT = {"afl": HLR_FMT_AFL_APLR, "fp64": HLR_FMT_FP64, "aflp": B.HLR_FMT_AFLP, "bfl": B.HLR_FMT_BFL,
+        "dfl": B.HLR_FMT_DFL, HLR_FMT_AFL_APLR: HLR_FMT_AFL_APLR, HLR_FMT_FP64: HLR_FMT_FP64,
+        B.HLR_FMT_AFLP: B.HLR_FMT_AFLP, B.HLR_FMT_BFL: B.HLR_FMT_BFL, B.HLR_FMT_DFL: B.HLR_FMT_DFL}
 _KERNEL = {"exp2d": HLR_KERNEL_EXP, "exp": HLR_KERNEL_EXP, "laplace": HLR_KERNEL_LAPLACE,
            "matern15": HLR_KERNEL_MATERN15}
 
@@ -299,6 +301,22 @@ def build_kernel_hmatrix(points: np.ndarray, kernel: str, eps: float, scale: flo
     out = C.c_void_p(0)
     B.check(B.lib.hlr_build(C.byref(prob), C.byref(out)))
     return HostHMatrix(out.value, P)
+
+
+def encode(a: np.ndarray, u: float, fmt: str = "afl"):
+    """Host encoder of the library for any compressed format (afl, aflp, bfl, dfl): returns
+    (m_min, e, m, stream bytes padded to 16)."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    m_min = C.c_double(0)
+    e = C.c_int32(0)
+    m = C.c_int32(0)
+    nbytes = C.c_size_t(0)
+    cap = (a.size * 64 + 7) // 8 + 32
+    buf = np.zeros(cap, dtype=np.uint8)
+    f = _FMT[fmt] if fmt in _FMT else int(fmt)
+    B.check(B.lib.hlr_encode(f, B.f64ptr(a), a.size, float(u), C.byref(m_min), C.byref(e), C.byref(m),
+                             buf.ctypes.data, cap, C.byref(nbytes)))
+    return m_min.value, e.value, m.value, buf[: nbytes.value].tobytes()
 
 
 def afl_encode(a: np.ndarray, u: float):

@@ -1,4 +1,5 @@
-// Host AFL encoder (Section 3.2) and the hlr_afl_encode entry point.
+// Host AFL encoder (Section 3.2), its byte-aligned variants (AFLP, BFL, DFL) and the
+// hlr_afl_encode / hlr_encode entry points.
 //
 // One unit of n values is stored as follows. m_min is the smallest nonzero magnitude; every
 // magnitude is scaled by 1/m_min and shifted by +1 (the remark of Section 3.2), giving v >= 2
@@ -7,6 +8,10 @@
 // the unbiased exponent of v (>= 0) in e bits, e the smallest width that holds the largest
 // field. The code of value j is sign | field | mantissa (sign on top), w = 1 + e + m bits,
 // placed at stream bits [j w, (j+1) w), LSB-first, zero-padded to 16 bytes.
+// AFLP raises m to the smallest m' for which 1 + e + m' is a multiple of 8. BFL stores the top
+// 1 + 8 + m' bits of the FP32 pattern of the value (cast to nearest, then rounded half up to
+// m' in {7, 15, 23}); DFL the top 1 + 11 + m' bits of the FP64 pattern rounded half up to
+// m' in {4, 12, ..., 52}.
 // Compiled with -ffp-contract=off: every FP64 operation is a separately rounded IEEE op.
 #include <cmath>
 #include <cstring>
@@ -48,8 +53,13 @@ static inline int bit_length(uint64_t x) {
   return l;
 }
 
-bool afl_params(const double *a, int64_t n, double u, AflParams *p) {
-  p->m = mantissa_bits(u);
+static bool afl_params_m(const double *a, int64_t n, int m, AflParams *p);
+
+bool afl_params(const double *a, int64_t n, double u, AflParams *p) { return afl_params_m(a, n, mantissa_bits(u), p); }
+
+static bool afl_params_m(const double *a, int64_t n, int m, AflParams *p) {
+  p->kind = VF_AFL;
+  p->m = m;
   double m_min = INFINITY;
   for (int64_t j = 0; j < n; ++j) {
     double x = a[j];
@@ -97,7 +107,103 @@ void afl_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out) {
   }
 }
 
+static inline uint32_t fbits(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  return b;
+}
+
+bool unit_params(int fmt, const double *a, int64_t n, double u, AflParams *p) {
+  const int m = mantissa_bits(u);
+  if (fmt == HLR_FMT_AFL_APLR) return afl_params_m(a, n, m, p);
+  if (fmt == HLR_FMT_AFLP) {
+    for (int mm = m;; ++mm) {
+      if (!afl_params_m(a, n, mm, p)) return false;
+      if (p->w % 8 == 0 || mm == 52) return true;
+    }
+  }
+  if (fmt == HLR_FMT_BFL) {
+    const int mp = m <= 7 ? 7 : m <= 15 ? 15 : 23;
+    for (int64_t j = 0; j < n; ++j) {
+      const float x = float(a[j]);
+      if (!std::isfinite(a[j]) || !std::isfinite(x)) return false;
+      uint64_t b = fbits(x);
+      if (mp < 23) b = (b + (uint64_t(1) << (22 - mp))) & ~((uint64_t(1) << (23 - mp)) - 1);
+      if (((b >> 23) & 0xFF) == 0xFF) return false;
+    }
+    p->kind = VF_BFL;
+    p->m_min = 1.0;
+    p->e = 8;
+    p->m = mp;
+    p->w = 9 + mp;
+    return true;
+  }
+  if (fmt == HLR_FMT_DFL) {
+    int mp = 4;
+    while (mp < m) mp += 8;
+    for (int64_t j = 0; j < n; ++j) {
+      if (!std::isfinite(a[j])) return false;
+      if (((round_bits(a[j], mp) >> 52) & 0x7FF) == 0x7FF) return false;
+    }
+    p->kind = VF_DFL;
+    p->m_min = 1.0;
+    p->e = 11;
+    p->m = mp;
+    p->w = 12 + mp;
+    return true;
+  }
+  return false;
+}
+
+void unit_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out) {
+  if (p.kind == VF_AFL) {
+    afl_pack(a, n, p, out);
+    return;
+  }
+  uint64_t *words = reinterpret_cast<uint64_t *>(out);
+  const int w = p.w;
+  for (int64_t j = 0; j < n; ++j) {
+    uint64_t code;
+    if (p.kind == VF_BFL) {
+      uint64_t b = fbits(float(a[j]));
+      if (p.m < 23) b = (b + (uint64_t(1) << (22 - p.m))) & ~((uint64_t(1) << (23 - p.m)) - 1);
+      code = b >> (23 - p.m);
+    } else {
+      code = round_bits(a[j], p.m) >> (52 - p.m);
+    }
+    const uint64_t bit = uint64_t(j) * uint64_t(w);
+    const uint64_t wi = bit >> 6;
+    const unsigned off = unsigned(bit & 63);
+    words[wi] |= code << off;
+    if (off + unsigned(w) > 64) words[wi + 1] |= code >> (64 - off);
+  }
+}
+
 }  // namespace hlr
+
+extern "C" int hlr_encode(int32_t fmt, const double *a, int64_t n, double u, double *m_min, int32_t *e, int32_t *m,
+                          uint8_t *out, size_t cap, size_t *nbytes) {
+  using namespace hlr;
+  if (n < 0 || (n > 0 && !a) || !m_min || !e || !m || !nbytes)
+    return set_error(HLR_ERR_INVALID, "hlr_encode: null argument or negative n");
+  if (!(u > 0.0) || !std::isfinite(u))
+    return set_error(HLR_ERR_INVALID, "hlr_encode: precision must be positive and finite");
+  if (fmt != HLR_FMT_AFL_APLR && fmt != HLR_FMT_AFLP && fmt != HLR_FMT_BFL && fmt != HLR_FMT_DFL)
+    return set_error(HLR_ERR_INVALID, "hlr_encode: unknown format");
+  AflParams p;
+  if (!unit_params(fmt, a, n, u, &p)) return set_error(HLR_ERR_INVALID, "hlr_encode: value not representable");
+  const size_t need = padded16(afl_bytes(n, p.w));
+  *m_min = p.m_min;
+  *e = p.e;
+  *m = p.m;
+  *nbytes = need;
+  if (cap < need) return set_error(HLR_ERR_OOM, "hlr_encode: output buffer too small");
+  if (need == 0) return HLR_OK;
+  std::vector<uint64_t> tmp(need / 8 + 1, 0);
+  unit_pack(a, n, p, reinterpret_cast<uint8_t *>(tmp.data()));
+  std::memcpy(out, tmp.data(), need);
+  return HLR_OK;
+}
 
 extern "C" int hlr_afl_encode(const double *a, int64_t n, double u, double *m_min, int32_t *e,
                               int32_t *m, uint8_t *out, size_t cap, size_t *nbytes) {

@@ -37,7 +37,12 @@
 
 namespace hlr {
 
-enum { FMT_AFL32 = 0, FMT_AFL64 = 1, FMT_RAW64 = 2 };
+// Kernel formats: the stored values (AFL family, BFL, DFL, plain FP64) and the accumulation.
+enum { FMT_AFL32 = 0, FMT_AFL64 = 1, FMT_RAW64 = 2, FMT_BFL32 = 3, FMT_DFL32 = 4 };
+template <int FMT>
+constexpr bool kFP32 = FMT == FMT_AFL32 || FMT == FMT_BFL32 || FMT == FMT_DFL32;
+template <int FMT>
+constexpr int kVF = FMT == FMT_BFL32 ? VF_BFL : FMT == FMT_DFL32 ? VF_DFL : VF_AFL;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kCWarps = kConsumers / 32;
 constexpr unsigned kFull = 0xffffffffu;
@@ -53,6 +58,10 @@ struct Tr<FMT_AFL32> {
   using A = float;
   static constexpr int esz = 4;
 };
+template <>
+struct Tr<FMT_BFL32> : Tr<FMT_AFL32> {};
+template <>
+struct Tr<FMT_DFL32> : Tr<FMT_AFL32> {};
 constexpr int kRB = 8;          // right-hand sides per pass of the multi-RHS product
 constexpr int kMaxBatch = 64;   // products per launch of the batched path
 
@@ -201,6 +210,47 @@ __device__ __forceinline__ double dec_f64(uint64_t code, const ColDec &c) {
   return ((code >> em) & 1ull) ? -v : v;
 }
 
+// BFL / DFL codes (Section 3.2): the code is the top of an FP32 / FP64 bit pattern, so it is
+// shifted back into place; the bits above the code leave the word. DFL as FP32 needs w <= 32.
+__device__ __forceinline__ float dec_bfl(uint32_t code, const ColDec &c) { return __uint_as_float(code << (23 - c.m)); }
+__device__ __forceinline__ float dec_dfl32(uint32_t code, const ColDec &c) {
+  return float(__hiloint2double(int(code << (20 - c.m)), 0));
+}
+// value of a code of any width and value format in FP64: AFL family +-(v - 1) (to be scaled by
+// m_min), BFL and DFL the stored value itself
+__device__ __forceinline__ double dec_any64(uint64_t code, const ColDec &c, int vf) {
+  if (vf == VF_BFL) return double(__uint_as_float(uint32_t(code << (23 - c.m))));
+  if (vf == VF_DFL) return __longlong_as_double(static_cast<long long>(code << (52 - c.m)));
+  return dec_f64(code, c);
+}
+// FP32 family: the value entering the phase-1 dot product, and value times multiplier
+template <int FMT>
+__device__ __forceinline__ float val32(uint32_t code, const ColDec &c) {
+  if constexpr (FMT == FMT_BFL32)
+    return dec_bfl(code, c);
+  else if constexpr (FMT == FMT_DFL32)
+    return dec_dfl32(code, c);
+  else
+    return dec_f32(code, c);
+}
+template <int FMT>
+__device__ __forceinline__ float valmul32(uint32_t code, const ColDec &c, float mult) {
+  if constexpr (FMT == FMT_AFL32)
+    return dec_mul_f32(code, c, mult);
+  else
+    return val32<FMT>(code, c) * mult;
+}
+// whether val32 applies to this column (else the FP64 decode of a 64-bit window)
+template <int FMT>
+__device__ __forceinline__ bool fast_dec(const ColDec &c) {
+  if constexpr (FMT == FMT_BFL32)
+    return true;
+  else if constexpr (FMT == FMT_DFL32)
+    return c.narrow;
+  else
+    return c.fast32;
+}
+
 // code (w <= 32) starting at an arbitrary bit of a shared-memory word array
 __device__ __forceinline__ uint32_t code32_at(const uint32_t *p, uint32_t bit) {
   const uint32_t q = bit >> 5;
@@ -329,11 +379,11 @@ __device__ bool produce(const DevLayout &L, uint32_t e0, uint32_t e1, uint8_t *s
   constexpr uint32_t esz = Tr<FMT>::esz;
   constexpr size_t slot = slot_bytes<FMT, PH, R>();
   const int lane = threadIdx.x & 31;
-  const uint8_t *xsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.xperm32)
+  const uint8_t *xsrc = kFP32<FMT> ? reinterpret_cast<const uint8_t *>(L.xperm32)
                                          : reinterpret_cast<const uint8_t *>(L.xperm64);
-  const uint8_t *tsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.tw32)
+  const uint8_t *tsrc = kFP32<FMT> ? reinterpret_cast<const uint8_t *>(L.tw32)
                                          : reinterpret_cast<const uint8_t *>(L.tw64);
-  const uint8_t *fsrc = FMT == FMT_AFL32 ? reinterpret_cast<const uint8_t *>(L.fac32)
+  const uint8_t *fsrc = kFP32<FMT> ? reinterpret_cast<const uint8_t *>(L.fac32)
                                          : reinterpret_cast<const uint8_t *>(L.fac64);
   const uint4 *ent = reinterpret_cast<const uint4 *>(L.ph[PH].ent);
   // the stream is read 32 entries per coalesced load, one load ahead
@@ -470,24 +520,25 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
           const ColDec c = col_dec(h.e, h.m);
           if (c.narrow) {
             uint32_t bit = 0;
-            if constexpr (FMT == FMT_AFL32) {
-              if (c.fast32) {
+            if constexpr (kFP32<FMT>) {
+              if (fast_dec<FMT>(c)) {
                 const uint32_t col_s = smem_u32(col);
                 const uint32_t xstep = uint32_t(xs) * 4u;
                 uint32_t xa = smem_u32(xr);
 #pragma unroll 8
                 for (int r = 0; r < rc; ++r, bit += c.w, xa += xstep)
-                  dot = fmaf(dec_f32(bc_code32_s(col_s, bit), c), ld_shared_f32(xa), dot);
+                  dot = fmaf(val32<FMT>(bc_code32_s(col_s, bit), c), ld_shared_f32(xa), dot);
               } else {
                 for (int r = 0; r < rc; ++r, bit += c.w)
-                  dot = fmaf(float(dec_f64(bc_code32(col, bit), c)), xr[r * xs], dot);
+                  dot = fmaf(float(dec_any64(bc_code32(col, bit), c, kVF<FMT>)), xr[r * xs], dot);
               }
             } else {
 #pragma unroll 4
-              for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(bc_code32(col, bit), c), xr[r * xs], dot);
+              for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_any64(bc_code32(col, bit), c, L.vfmt), xr[r * xs], dot);
             }
           } else {
-            for (int r = 0; r < rc; ++r) dot += A(dec_f64(bc_code64(col, uint32_t(r) * c.w), c)) * xr[r * xs];
+            const int vf = kFP32<FMT> ? kVF<FMT> : L.vfmt;
+            for (int r = 0; r < rc; ++r) dot += A(dec_any64(bc_code64(col, uint32_t(r) * c.w), c, vf)) * xr[r * xs];
           }
         }
       }
@@ -502,7 +553,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
       const Seg &sg = *sgp;
       const A f = aux[sg.fs + j];
       if (sg.x.nchunks == 1) {
-        if constexpr (FMT == FMT_AFL32)
+        if constexpr (kFP32<FMT>)
           L.tw32[sg.tidx + j] = dot * f;
         else
           L.tw64[sg.tidx + j] = dot * f;
@@ -530,7 +581,7 @@ __global__ void k_combine(const __grid_constant__ Jobs<NB> J) {
     double sum = 0.0;
     if constexpr (R == 1) {
       for (uint32_t k = 0; k < c.nchunks; ++k) sum += L.partial[size_t(c.pbase) + k];
-      if constexpr (FMT == FMT_AFL32)
+      if constexpr (kFP32<FMT>)
         L.tw32[c.tidx] = float(sum * double(L.fac32[c.tidx]));
       else
         L.tw64[c.tidx] = sum * L.fac64[c.tidx];
@@ -571,7 +622,7 @@ __device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const 
 // ---------------------------------------------------------------------------------------------
 // rows [0, nr) of the lane's slice into acc[r]; rows past the leaf decode the slice's first value
 // (in bounds) and are dropped. GEN: the generic FP64 decode (wide codes, large e or m).
-template <bool GEN>
+template <bool GEN, int FMT>
 __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t *col, const ColDec &c, float mult) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -579,23 +630,25 @@ __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t
     if (!GEN && 16 * k + 16 <= nr) {  // a whole chunk of the leaf: no row checks
       uint32_t bit = uint32_t(16 * k) * c.w;
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr, bit += c.w) acc[16 * k + rr] += dec_mul_f32(bc_code32(col, bit), c, mult);
+      for (int rr = 0; rr < 16; ++rr, bit += c.w) acc[16 * k + rr] += valmul32<FMT>(bc_code32(col, bit), c, mult);
     } else {
 #pragma unroll
       for (int rr = 0; rr < 16; ++rr) {
         const int r = 16 * k + rr;
         const bool ok = r < nr;
         const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
-        const float p = GEN ? float(dec_f64(bc_code64(col, bit), c)) * mult : dec_mul_f32(bc_code32(col, bit), c, mult);
+        const float p = GEN ? float(dec_any64(bc_code64(col, bit), c, kVF<FMT>)) * mult
+                            : valmul32<FMT>(bc_code32(col, bit), c, mult);
         if (ok) acc[r] += p;
       }
     }
   }
 }
 
+template <int FMT>
 __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                    uint64_t *empty, double *red, double *__restrict__ y, uint32_t &parity) {
-  constexpr size_t slot = slot_bytes<FMT_AFL32, 1>();
+  constexpr size_t slot = slot_bytes<FMT, 1>();
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   float acc[64];
 #pragma unroll
@@ -623,10 +676,11 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
         yold = y[gi];
       }
     }
-    // idle lanes decode e = m = 0 codes (value 0) times a zero multiplier from the header words
+    // idle lanes (no slice) skip the rows
     float mult = 0.f;
     uint32_t e = 0, m = 0;
     const uint32_t *col = Wd;
+    bool active = false;
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
@@ -635,13 +689,17 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
         e = h.e;
         m = h.m;
         col = Wd + bc_column(ph, t);
+        active = true;
       }
     }
     const ColDec c = col_dec(e, m);
-    if (__all_sync(kFull, c.fast32))  // the FP32 bit-pattern decode for the whole warp
-      p2_rows<false>(acc, nr, col, c, mult);
-    else
-      p2_rows<true>(acc, nr, col, c, mult);
+    const bool fast = __all_sync(kFull, !active || fast_dec<FMT>(c));  // FP32 bit-pattern decode
+    if (active) {
+      if (fast)
+        p2_rows<false, FMT>(acc, nr, col, c, mult);
+      else
+        p2_rows<true, FMT>(acc, nr, col, c, mult);
+    }
     if (flags & PF_END_LEAF) {
       // reduce-scatter over the warp: 5 halving stages (stage s keeps the upper half of the
       // vector when lane bit 4 - s is set); afterwards lane l holds the sums of rows 2l, 2l + 1
@@ -715,10 +773,11 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
         yold = y[gi];
       }
     }
-    // idle lanes decode e = m = 0 codes (value 0) times a zero multiplier from the header words
+    // idle lanes (no slice) write zeros
     A mult = A(0);
     uint32_t e = 0, m = 0;
     const uint32_t *col = Wd;
+    bool active = false;
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
@@ -727,6 +786,7 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
         e = h.e;
         m = h.m;
         col = Wd + bc_column(ph, t);
+        active = true;
       }
     }
     const ColDec c = col_dec(e, m);
@@ -750,11 +810,15 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
             tile[rr * 33 + lane] = float(dec_f64(bc_code64(col, bit0 + rr * c.w), c)) * mult;
         }
       } else {
-        if (c.narrow) {
+        if (!active) {
+          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = A(0);
+        } else if (c.narrow) {
 #pragma unroll 4
-          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_f64(bc_code32(col, bit0 + rr * c.w), c) * mult;
+          for (int rr = 0; rr < rows; ++rr)
+            tile[rr * 33 + lane] = dec_any64(bc_code32(col, bit0 + rr * c.w), c, L.vfmt) * mult;
         } else {
-          for (int rr = 0; rr < rows; ++rr) tile[rr * 33 + lane] = dec_f64(bc_code64(col, bit0 + rr * c.w), c) * mult;
+          for (int rr = 0; rr < rows; ++rr)
+            tile[rr * 33 + lane] = dec_any64(bc_code64(col, bit0 + rr * c.w), c, L.vfmt) * mult;
         }
       }
       __syncwarp();
@@ -1104,8 +1168,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__
         ok = consume_phase2_multi(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
     } else if constexpr (PH == 0) {
       ok = consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
-    } else if constexpr (FMT == FMT_AFL32) {
-      ok = consume_phase2_reg(jb.L, np, it, smem, full, empty, red, jb.y, parity);
+    } else if constexpr (kFP32<FMT>) {
+      ok = consume_phase2_reg<FMT>(jb.L, np, it, smem, full, empty, red, jb.y, parity);
     } else if constexpr (FMT == FMT_AFL64) {
       ok = consume_phase2<FMT>(jb.L, np, it, smem, full, empty, red, tiles, jb.y, parity);
     } else {
@@ -1147,9 +1211,19 @@ __global__ void k_decode_stream(const uint32_t *words, int64_t n, double m_min, 
   }
 }
 
+// exact FP64 value of a code in value format vf (the decode of Section 3.2 for AFL, the FP32 /
+// FP64 pattern for BFL / DFL)
+__device__ double decode_exact_vf(uint64_t code, int e, int m, double m_min, int vf) {
+  const int w = 1 + e + m;
+  if (w < 64) code &= (1ull << w) - 1ull;
+  if (vf == VF_BFL) return double(__uint_as_float(uint32_t(code << (23 - m))));
+  if (vf == VF_DFL) return __longlong_as_double(static_cast<long long>(code << (52 - m)));
+  return decode_code_exact(code, e, m, m_min);
+}
+
 __global__ void k_decode_slices(const uint8_t *base, const uint64_t *src, const uint64_t *dst, const uint32_t *nv,
                                 const uint32_t *unit, const double *mmin, const uint8_t *ue, const uint8_t *um,
-                                int64_t nslices, int raw, double *out) {
+                                int64_t nslices, int raw, int vf, double *out) {
   for (int64_t s = blockIdx.x; s < nslices; s += gridDim.x) {
     const uint32_t u = unit[s];
     const int e = ue[u], m = um[u];
@@ -1169,13 +1243,13 @@ __global__ void k_decode_slices(const uint8_t *base, const uint64_t *src, const 
         const uint32_t sh = uint32_t(bit & 31);
         const uint32_t a = col[32 * q], b = col[32 * q + 32], c = col[32 * q + 64];
         const uint64_t code = (uint64_t(__funnelshift_r(b, c, sh)) << 32) | __funnelshift_r(a, b, sh);
-        out[dst[s] + uint64_t(v) * step] = decode_code_exact(code, e, m, mmin[u]);
+        out[dst[s] + uint64_t(v) * step] = decode_exact_vf(code, e, m, mmin[u], vf);
       } else {
         const uint64_t bit = b0 + uint64_t(v) * uint64_t(w);
         const uint32_t *wp = reinterpret_cast<const uint32_t *>(base) + (bit >> 5);
         const uint32_t sh = uint32_t(bit & 31);
         const uint64_t code = (uint64_t(__funnelshift_r(wp[1], wp[2], sh)) << 32) | __funnelshift_r(wp[0], wp[1], sh);
-        out[dst[s] + v] = decode_code_exact(code, e, m, mmin[u]);
+        out[dst[s] + v] = decode_exact_vf(code, e, m, mmin[u], vf);
       }
     }
   }
@@ -1208,6 +1282,10 @@ void set_smem_attrs() {
   set_smem_attr<FMT_RAW64, 1, 1, NB>();
   set_smem_attr<FMT_AFL32, 0, kRB, NB>();
   set_smem_attr<FMT_AFL32, 1, kRB, NB>();
+  set_smem_attr<FMT_BFL32, 0, 1, NB>();
+  set_smem_attr<FMT_BFL32, 1, 1, NB>();
+  set_smem_attr<FMT_DFL32, 0, 1, NB>();
+  set_smem_attr<FMT_DFL32, 1, 1, NB>();
 }
 
 const DevProps &props(int dev) {
@@ -1315,10 +1393,14 @@ int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream
   J.j[0] = single_job(H, x, y);
   if (H.L.raw)
     launch_jobs<FMT_RAW64, 1, 1>(J, st, ev);
-  else if (acc == HLR_ACC_FP32)
-    launch_jobs<FMT_AFL32, 1, 1>(J, st, ev);
+  else if (acc != HLR_ACC_FP32)
+    launch_jobs<FMT_AFL64, 1, 1>(J, st, ev);  // FP64 decode of every value format
+  else if (H.L.vfmt == VF_BFL)
+    launch_jobs<FMT_BFL32, 1, 1>(J, st, ev);
+  else if (H.L.vfmt == VF_DFL)
+    launch_jobs<FMT_DFL32, 1, 1>(J, st, ev);
   else
-    launch_jobs<FMT_AFL64, 1, 1>(J, st, ev);
+    launch_jobs<FMT_AFL32, 1, 1>(J, st, ev);
   return cuda_status("hlr_matvec: launch");
 }
 
@@ -1390,12 +1472,14 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   const bool fp32 = (flags & 0xff) == HLR_ACC_FP32;
   const int multi_from = (flags & HLR_MULTI) ? 1 : 2;  // fewest columns that take the multi-RHS kernels
   Batcher<FMT_AFL32, 1> b32(st);
+  Batcher<FMT_BFL32, 1> bbfl(st);
+  Batcher<FMT_DFL32, 1> bdfl(st);
   Batcher<FMT_AFL64, 1> b64(st);
   Batcher<FMT_RAW64, 1> braw(st);
-  Batcher<FMT_AFL32, kRB> bm(st);
+  Batcher<FMT_AFL32, kRB> bm(st);  // multi-column passes decode the AFL family only
   // pass scratch first (growing it frees the old one, which no pending product may still use)
   for (int q = 0; q < nreq; ++q) {
-    if (nrhs[q] < multi_from || !fp32 || H[q]->L.raw) continue;
+    if (nrhs[q] < multi_from || !fp32 || H[q]->L.raw || H[q]->L.vfmt != VF_AFL) continue;
     int passes = 0;
     for (int k = 0; k < nreq; ++k)
       if (H[k] == H[q] && nrhs[k] >= multi_from) passes = std::max(passes, (nrhs[k] + kRB - 1) / kRB);
@@ -1408,7 +1492,7 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
     Handle &Hq = *H[q];
     const int r = nrhs[q];
     if (r <= 0) continue;
-    if (r >= multi_from && fp32 && !Hq.L.raw) {
+    if (r >= multi_from && fp32 && !Hq.L.raw && Hq.L.vfmt == VF_AFL) {
       const int passes = (r + kRB - 1) / kRB;
       float *xp, *tw;
       double *part;
@@ -1429,14 +1513,20 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
         const Job jb = single_job(Hq, X[q] + size_t(c) * size_t(ldx[q]), Y[q] + size_t(c) * size_t(ldy[q]));
         if (Hq.L.raw)
           braw.add(&Hq, -1, jb);
-        else if (fp32)
-          b32.add(&Hq, -1, jb);
-        else
+        else if (!fp32)
           b64.add(&Hq, -1, jb);
+        else if (Hq.L.vfmt == VF_BFL)
+          bbfl.add(&Hq, -1, jb);
+        else if (Hq.L.vfmt == VF_DFL)
+          bdfl.add(&Hq, -1, jb);
+        else
+          b32.add(&Hq, -1, jb);
       }
     }
   }
   b32.flush();
+  bbfl.flush();
+  bdfl.flush();
   b64.flush();
   braw.flush();
   bm.flush();
@@ -1486,7 +1576,7 @@ int launch_decode_units(const Handle &H, double *out, void *stream) {
   cudaMemcpyAsync(d_e, H.unit_e.data(), nu, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(d_m, H.unit_m.data(), nu, cudaMemcpyHostToDevice, st);
   const int grid = int(std::min<int64_t>(ns, 65535));
-  k_decode_slices<<<grid, 64, 0, st>>>(H.L.base, d_src, d_dst, d_n, d_unit, d_mmin, d_e, d_m, ns, H.L.raw, out);
+  k_decode_slices<<<grid, 64, 0, st>>>(H.L.base, d_src, d_dst, d_n, d_unit, d_mmin, d_e, d_m, ns, H.L.raw, H.L.vfmt, out);
   int rc = cuda_status("hlr_decode_units");
   cudaError_t e = cudaStreamSynchronize(st);
   cudaFree(tmp);
@@ -1570,7 +1660,7 @@ int launch_decode_units_static(const Handle &H, double *out, void *stream) {
                                        reinterpret_cast<const uint32_t *>(base + o_n),
                                        reinterpret_cast<const uint32_t *>(base + o_unit),
                                        reinterpret_cast<const double *>(base + o_mmin), base + o_e, base + o_m, ns,
-                                       H.L.raw, out);
+                                       H.L.raw, H.L.vfmt, out);
   return cuda_status("hlr_decode_units_static");
 }
 

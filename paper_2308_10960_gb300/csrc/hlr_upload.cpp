@@ -72,21 +72,22 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   const int64_t n = d->n;
   if (n <= 0 || n > (int64_t(1) << 31) - 64) return set_error(HLR_ERR_INVALID, "hlr_upload: n out of range");
   if (d->nblocks <= 0 || !d->blocks) return set_error(HLR_ERR_INVALID, "hlr_upload: no blocks");
-  if (d->format != HLR_FMT_AFL_APLR && d->format != HLR_FMT_FP64)
+  if (d->format != HLR_FMT_AFL_APLR && d->format != HLR_FMT_FP64 && d->format != HLR_FMT_AFLP &&
+      d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
   int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
   if (d->tuning != 0) {
     const int sl = d->tuning & 15, ll = (d->tuning >> 4) & 15, kb = (d->tuning >> 8) & 255;
-    if (d->format != HLR_FMT_AFL_APLR || sl < 5 || sl > 7 || ll < 5 || ll > 6 || kb < 4 || kb > kPieceMax / 1024 ||
+    if (d->format == HLR_FMT_FP64 || sl < 5 || sl > 7 || ll < 5 || ll > 6 || kb < 4 || kb > kPieceMax / 1024 ||
         (d->tuning >> 16) != 0)
       return set_error(HLR_ERR_INVALID, "hlr_upload: bad tuning (see HLR_TUNING; AFL format only)");
     sub_rows = 1 << sl;
     leaf_rows = 1 << ll;
     piece_max = kb * 1024;
   }
-  if (d->format == HLR_FMT_AFL_APLR && !(d->eps > 0.0 && d->eps < 1.0))
+  const bool afl = d->format != HLR_FMT_FP64;  // one of the compressed formats
+  if (afl && !(d->eps > 0.0 && d->eps < 1.0))
     return set_error(HLR_ERR_INVALID, "hlr_upload: eps must be in (0, 1)");
-  const bool afl = d->format == HLR_FMT_AFL_APLR;
 
   // ---- permutation
   std::vector<int64_t> perm(n);
@@ -201,14 +202,14 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
   for (int64_t u = 0; u < nunits; ++u) {
     if (afl) {
-      if (!afl_params(usrc[u], in.unit_len[u], uprec[u], &in.prm[u])) bad |= 1;
+      if (!unit_params(d->format, usrc[u], in.unit_len[u], uprec[u], &in.prm[u])) bad |= 1;
     } else {
       for (int64_t j = 0; j < in.unit_len[u]; ++j)
         if (!std::isfinite(usrc[u][j])) bad |= 1;
-      in.prm[u] = AflParams{1.0, 0, 0, 64};
+      in.prm[u] = AflParams{1.0, 0, 0, 64, VF_AFL};
     }
   }
-  if (bad) return set_error(HLR_ERR_INVALID, "hlr_upload: NaN or Inf in block data");
+  if (bad) return set_error(HLR_ERR_INVALID, "hlr_upload: NaN or Inf in block data (or beyond the format's range)");
   in.uoff.assign(nunits + 1, 0);
   uint64_t stream_bytes = 0;
   for (int64_t u = 0; u < nunits; ++u) {
@@ -225,7 +226,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     uint8_t *dst = canon.p + in.uoff[u];
     std::memset(dst, 0, in.uoff[u + 1] - in.uoff[u]);
     if (afl)
-      afl_pack(usrc[u], in.unit_len[u], in.prm[u], dst);
+      unit_pack(usrc[u], in.unit_len[u], in.prm[u], dst);
     else
       std::memcpy(dst, usrc[u], size_t(in.unit_len[u]) * 8);
   }
@@ -385,6 +386,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   L.n = n;
   L.ncnt = int32_t(po.ncnt);
   L.raw = afl ? 0 : 1;
+  L.vfmt = d->format == HLR_FMT_BFL ? VF_BFL : d->format == HLR_FMT_DFL ? VF_DFL : VF_AFL;
   H->nunits = nunits;
   H->values = values;
   H->part_total = po.part_total;

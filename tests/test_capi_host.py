@@ -161,3 +161,23 @@ def test_autotuner_rank_classes():
     assert t.lookup({"rank_sum": 100, "nlowrank": 10}) is None
     t.table[(8, 1)] = (32, 64, 16)
     assert t.lookup({"rank_sum": 100, "nlowrank": 10}) == hg.tuning_code(32, 64, 16)
+
+
+@pytest.mark.parametrize("fmt", ["afl", "aflp", "bfl", "dfl"])
+@pytest.mark.parametrize("u", [0.5, 1e-2, 2.0 ** -9, 1e-6, 1e-9, 2.0 ** -60])
+def test_host_encoder_all_formats_byte_exact(fmt, u):
+    """hlr_encode writes exactly the oracle's stream for AFL and its aligned variants."""
+    g = np.random.default_rng(21)
+    for a in (g.standard_normal(333) * np.exp(g.uniform(-12, 12, 333)), np.zeros(7),
+              np.array([0.0, -1.5, 3.0, -0.0, 1e-30])):
+        ref = afl.encode(a, u, fmt)
+        mm, e, m, data = hg.encode(a, u, fmt)
+        assert (e, m) == (ref.e, ref.m) and mm == ref.m_min, (fmt, u)
+        assert data == ref.data, (fmt, u)
+
+
+def test_host_encoder_rejects_values_outside_bfl():
+    with pytest.raises(hg.HlrError):
+        hg.encode(np.array([1e300]), 1e-6, "bfl")
+    with pytest.raises(hg.HlrError):
+        hg.encode(np.array([1.0]), 1e-6, 9)
