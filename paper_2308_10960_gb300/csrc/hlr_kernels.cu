@@ -210,11 +210,22 @@ __device__ __forceinline__ double dec_f64(uint64_t code, const ColDec &c) {
   return ((code >> em) & 1ull) ? -v : v;
 }
 
+// Decode parameters of a lane: e and m from its header; bit 7 of the header's e marks a DFL
+// slice whose values are all FP32 normal numbers (the packer checks), decoded with integer ops.
+__device__ __forceinline__ ColDec lane_dec(const LaneHdr &h) {
+  ColDec c = col_dec(h.e & 0x7fu, h.m);
+  if (h.e & 0x80u) c.fast32 = c.narrow;
+  return c;
+}
+
 // BFL / DFL codes (Section 3.2): the code is the top of an FP32 / FP64 bit pattern, so it is
 // shifted back into place; the bits above the code leave the word. DFL as FP32 needs w <= 32.
 __device__ __forceinline__ float dec_bfl(uint32_t code, const ColDec &c) { return __uint_as_float(code << (23 - c.m)); }
+// (slices marked by the packer: all values FP32 normal numbers; rebias the exponent 1023 -> 127
+// and widen the mantissa, exact)
 __device__ __forceinline__ float dec_dfl32(uint32_t code, const ColDec &c) {
-  return float(__hiloint2double(int(code << (20 - c.m)), 0));
+  const uint32_t x = code << (20 - c.m);
+  return __uint_as_float((((x & 0x7fffffffu) - 0x38000000u) << 3) | (x & 0x80000000u));
 }
 // value of a code of any width and value format in FP64: AFL family +-(v - 1) (to be scaled by
 // m_min), BFL and DFL the stored value itself
@@ -245,10 +256,8 @@ template <int FMT>
 __device__ __forceinline__ bool fast_dec(const ColDec &c) {
   if constexpr (FMT == FMT_BFL32)
     return true;
-  else if constexpr (FMT == FMT_DFL32)
-    return c.narrow;
   else
-    return c.fast32;
+    return c.fast32;  // DFL: set by lane_dec for marked slices
 }
 
 // code (w <= 32) starting at an arbitrary bit of a shared-memory word array
@@ -517,7 +526,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
           const A *xr = aux + sg.xs + sub;
           const int xs = int(G);
           const uint32_t *col = Wd + bc_column(ph, t);
-          const ColDec c = col_dec(h.e, h.m);
+          const ColDec c = lane_dec(h);
           if (c.narrow) {
             uint32_t bit = 0;
             if constexpr (kFP32<FMT>) {
@@ -678,7 +687,7 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
     }
     // idle lanes (no slice) skip the rows
     float mult = 0.f;
-    uint32_t e = 0, m = 0;
+    LaneHdr hd{0xff, 0, 0, 0};
     const uint32_t *col = Wd;
     bool active = false;
     if (t < int(ph->ncols)) {
@@ -686,13 +695,12 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
       if (h.seg != 0xff) {
         const Seg &sg = segs[h.seg];
         mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * float(sg.m_min) : aux[sg.xs + h.j];
-        e = h.e;
-        m = h.m;
+        hd = h;
         col = Wd + bc_column(ph, t);
         active = true;
       }
     }
-    const ColDec c = col_dec(e, m);
+    const ColDec c = lane_dec(hd);
     const bool fast = __all_sync(kFull, !active || fast_dec<FMT>(c));  // FP32 bit-pattern decode
     if (active) {
       if (fast)
@@ -783,7 +791,7 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
       if (h.seg != 0xff) {
         const Seg &sg = segs[h.seg];
         mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * A(sg.m_min) : aux[sg.xs + h.j];
-        e = h.e;
+        e = h.e & 0x7fu;
         m = h.m;
         col = Wd + bc_column(ph, t);
         active = true;
@@ -967,7 +975,7 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
         const float4 *xr = xp4 + (size_t(sg.gx) + sub) * (kRB / 4);
         const int xs = int(G) * (kRB / 4);
         const uint32_t *col = Wd + bc_column(ph, t);
-        const ColDec c = col_dec(h.e, h.m);
+        const ColDec c = lane_dec(h);
 #pragma unroll 4
         for (int r = 0; r < rc; ++r) {
           float v;
@@ -1074,7 +1082,7 @@ __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, u
         }
         mv[0] = lo.x; mv[1] = lo.y; mv[2] = lo.z; mv[3] = lo.w;
         mv[4] = hi.x; mv[5] = hi.y; mv[6] = hi.z; mv[7] = hi.w;
-        e = h.e;
+        e = h.e & 0x7fu;
         m = h.m;
         col = Wd + bc_column(ph, t);
       }

@@ -488,6 +488,18 @@ class BcBuilder {
       else
         gather_codes(in_.canon + in_.uoff[L.u], L.v0, L.step, L.nv, L.w, tmp.data());
       for (uint32_t k = 0; k < L.words; ++k) data[col + 32 * k] = tmp[k];
+      if (in_.prm[L.u].kind == VF_DFL && L.m <= 20 && L.nv > 0) {
+        // all values FP32 normal numbers (biased FP64 exponent 897..1150): integer decode
+        bool fast = true;
+        for (uint32_t v = 0; v < L.nv && fast; ++v) {
+          const uint64_t bit = uint64_t(v) * L.w;
+          const uint64_t code = ((uint64_t(tmp[bit >> 5]) | (uint64_t(tmp[(bit >> 5) + 1]) << 32)) >> (bit & 31)) &
+                                ((uint64_t(1) << L.w) - 1);
+          const uint32_t ex = uint32_t(code >> L.m) & 0x7ffu;
+          fast = ex >= 897 && ex <= 1150;
+        }
+        if (fast) lh[pos].e = uint8_t(lh[pos].e | 0x80);
+      }
       if (map_ && L.nv > 0) {
         f_.s_src.push_back((8 * start + 32 * uint64_t(data_w0 + col)) | kStridedSlice);
         f_.s_dst.push_back(uint64_t(uvoff_[L.u]) + L.v0);
