@@ -99,7 +99,7 @@ __host__ __device__ constexpr size_t slot_bytes() {
 // kRB x 4 rows x 33 floats (multi-RHS)
 template <int FMT, int R>
 __host__ __device__ constexpr size_t tile_bytes() {
-  return R > 1 ? size_t(kRB) * 4 * 33 * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
+  return R > 1 ? (size_t(16) * 36 + 32 * kRB) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
 }
 // dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers (single RHS:
 // two halves; multi-RHS: kRB sums per row and warp, sharing the space of the tiles)
@@ -1026,24 +1026,41 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 2 (FP32): one lane per column slice (its bank column); a value is decoded
-// once and multiplied by the kRB multipliers of its column (t m_min(W) of the pass, or the X row
-// of the column times m_min). Every 4 rows the lanes write their kRB x 4 products to a padded
-// tile and lane i sums row 4k + (i & 3) of right-hand side i >> 2 over the 32 columns; FP32 sums
-// over the <= 32 columns a warp takes from one piece, compensated FP32 pairs across pieces, FP64
-// for the sum over warps and into Y.
+// Multi-RHS pass, phase 2 on the tensor cores: per warp and piece, Y|leaf (rows x kRB) +=
+// W~(rows x 32 slices) T(32 slices x kRB) as mma.sync m16n8k8 TF32 products. Every lane decodes
+// its slice (its bank column) 16 rows at a time into a padded shared-memory tile, from which the
+// A fragments are read; the multipliers of the 32 slices form the B fragments. Each FP32 operand
+// is split into two TF32 parts (hi + lo) and the product is the sum of the four part products,
+// so the contraction keeps FP32 accuracy (the lo*lo term is below 2^-22 relative). The products
+// of a piece are accumulated in FP32 registers (C fragments), added to compensated FP32 pairs
+// across the pieces of the leaf, and summed over the warps in FP64 into Y.
 // ---------------------------------------------------------------------------------------------
-__device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
-                                     uint64_t *empty, float *tiles) {
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                         uint64_t *empty, float *tiles) {
   const DevLayout &L = jb.L;
   constexpr size_t slot = slot_bytes<FMT_AFL32, 1, kRB>();
+  constexpr int kTS = 36;  // tile row stride (floats): conflict-free stores by lane and fragment loads
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int g = lane >> 2, tq = lane & 3;  // mma fragment coordinates
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
-  float *tile = tiles + warp * (kRB * 4 * 33);
-  double *red = reinterpret_cast<double *>(tiles);  // used at the end of a leaf, after a barrier
-  const int qi = lane >> 2, ri = lane & 3;           // this lane's (rhs, row) of each 4-row chunk
-  Comp32 acc[16];
+  float *tile = tiles + warp * (16 * kTS + 32 * kRB);
+  float *mbuf = tile + 16 * kTS;                      // [32 slices][kRB] multipliers of the warp
+  double *red = reinterpret_cast<double *>(tiles);    // used at the end of a leaf, after a barrier
+  Comp32 acc[4][4];  // per 16-row tile: C fragment (rows g, g + 8; columns 2 tq, 2 tq + 1)
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -1058,18 +1075,19 @@ __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, u
     const uint32_t flags = ph->flags;
     if (flags & PF_START_LEAF) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k].reset();
-    }
-    float mv[kRB];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) mv[q] = 0.f;
-    uint32_t e = 0, m = 0;
+        for (int b = 0; b < 4; ++b) acc[a][b].reset();
+    }
+    // the lane's slice and its kRB multipliers (zero for idle lanes)
+    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    LaneHdr hd{0xff, 0, 0, 0};
     const uint32_t *col = Wd;
+    bool active = false;
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
         const Seg &sg = segs[h.seg];
-        float4 lo, hi;
         if (sg.kind == SEG_DENSE) {
           const float mm = float(sg.m_min);
           const float4 x0 = __ldg(xp4 + (size_t(sg.gx) + h.j) * (kRB / 4));
@@ -1080,45 +1098,73 @@ __device__ bool consume_phase2_multi(const Job &jb, uint32_t np, uint32_t &it, u
           lo = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4));
           hi = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4) + 1);
         }
-        mv[0] = lo.x; mv[1] = lo.y; mv[2] = lo.z; mv[3] = lo.w;
-        mv[4] = hi.x; mv[5] = hi.y; mv[6] = hi.z; mv[7] = hi.w;
-        e = h.e & 0x7fu;
-        m = h.m;
+        hd = h;
         col = Wd + bc_column(ph, t);
+        active = true;
       }
     }
-    const ColDec c = col_dec(e, m);
+    reinterpret_cast<float4 *>(mbuf)[lane * 2] = lo;
+    reinterpret_cast<float4 *>(mbuf)[lane * 2 + 1] = hi;
+    __syncwarp();
+    // B fragments of the four 8-slice groups: B[k][n] = multiplier n of slice 8 kg + k
+    uint32_t bh[4][2], bl[4][2];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {  // 4-row chunks
-      const int r0 = 4 * k;
-      if (r0 >= nr) break;
+    for (int kg = 0; kg < 4; ++kg) {
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        const uint32_t bit = uint32_t(r0 + rr) * c.w;
-        float v = 0.f;
-        if (r0 + rr < nr) {
-          if (c.fast32)
-            v = dec_f32(bc_code32(col, bit), c);
-          else if (c.narrow)
-            v = float(dec_f64(bc_code32(col, bit), c));
-          else
-            v = float(dec_f64(bc_code64(col, bit), c));
-        }
+      for (int h2 = 0; h2 < 2; ++h2) {
+        const float bv = mbuf[(8 * kg + tq + 4 * h2) * kRB + g];
+        bh[kg][h2] = tf32_of(bv);
+        bl[kg][h2] = tf32_of(bv - __uint_as_float(bh[kg][h2]));
+      }
+    }
+    const ColDec c = lane_dec(hd);
+    const bool fast = __all_sync(kFull, !active || c.fast32);
 #pragma unroll
-        for (int q = 0; q < kRB; ++q) tile[(q * 4 + rr) * 33 + lane] = v * mv[q];
+    for (int mt = 0; mt < 4; ++mt) {  // 16-row tiles of the leaf
+      if (16 * mt >= nr) break;
+      // this lane's slice, rows 16 mt .. + 15 (rows past the leaf and idle lanes give 0)
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const int r = 16 * mt + rr;
+        const bool ok = active && r < nr;
+        const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
+        float v;
+        if (fast)
+          v = dec_f32(bc_code32(col, bit), c);
+        else
+          v = float(dec_any64(bc_code64(col, bit), c, VF_AFL));
+        tile[rr * kTS + lane] = ok ? v : 0.f;
       }
       __syncwarp();
-      float sum = 0.f;
-      const float *tr = tile + lane * 33;  // row (qi, ri) of the tile is row `lane`
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) sum += tr[cc];
-      acc[k].add(sum);
-      __syncwarp();
+      for (int kg = 0; kg < 4; ++kg) {
+        const float av[4] = {tile[g * kTS + 8 * kg + tq], tile[(g + 8) * kTS + 8 * kg + tq],
+                             tile[g * kTS + 8 * kg + tq + 4], tile[(g + 8) * kTS + 8 * kg + tq + 4]};
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[q] = tf32_of(av[q]);
+          al[q] = tf32_of(av[q] - __uint_as_float(ah[q]));
+        }
+        mma_tf32(d, al, bl[kg][0], bl[kg][1]);
+        mma_tf32(d, al, bh[kg][0], bh[kg][1]);
+        mma_tf32(d, ah, bl[kg][0], bl[kg][1]);
+        mma_tf32(d, ah, bh[kg][0], bh[kg][1]);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[mt][q].add(d[q]);
+      __syncwarp();  // the tile is rewritten for the next rows
     }
     if (flags & PF_END_LEAF) {
       bar_consumers();  // every warp is done with its tile before the sums reuse the space
 #pragma unroll
-      for (int k = 0; k < 16; ++k) red[(warp * 64 + 4 * k + ri) * kRB + qi] = acc[k].value();
+      for (int mt = 0; mt < 4; ++mt) {
+        red[(warp * 64 + 16 * mt + g) * kRB + 2 * tq] = acc[mt][0].value();
+        red[(warp * 64 + 16 * mt + g) * kRB + 2 * tq + 1] = acc[mt][1].value();
+        red[(warp * 64 + 16 * mt + g + 8) * kRB + 2 * tq] = acc[mt][2].value();
+        red[(warp * 64 + 16 * mt + g + 8) * kRB + 2 * tq + 1] = acc[mt][3].value();
+      }
       bar_consumers();
       const uint32_t row0 = ph->row0;
       for (int idx = t; idx < nr * jb.nrhs; idx += kConsumers) {
@@ -1173,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__
       if constexpr (PH == 0)
         ok = consume_phase1_multi(jb, np, it, smem, full, empty);
       else
-        ok = consume_phase2_multi(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
+        ok = consume_phase2_multi_mma(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
     } else if constexpr (PH == 0) {
       ok = consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
     } else if constexpr (kFP32<FMT>) {
