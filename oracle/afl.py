@@ -40,6 +40,12 @@ Byte-aligned variants (Section 3.2, after AFL):
 * DFL: 11 exponent bits, the FP64 layout: the FP64 pattern rounded half up to m' mantissa
   bits, m' the smallest of 4, 12, ..., 52 with m' >= m, top 1 + 11 + m' bits stored.
   BFL and DFL store no m_min (it is 1) and e is the fixed exponent width.
+
+Mixed precision comparison format MP-D-S-H (Section 3.3, after [AmeBoiBut:2022]): every column i
+of a lowrank factor is stored in the cheapest of FP16, FP32, FP64 whose unit roundoff
+(Table 1: 2^-11, 2^-24, 2^-53) is <= its APLR precision u~_i = delta / sigma_i; values are cast
+to that format with round to nearest even; dense leaves stay FP64 (the comparison compresses
+only lowrank factors). A unit is tagged mp16 / mp32 / mp64 and e is the format's exponent width.
 """
 from __future__ import annotations
 
@@ -70,7 +76,8 @@ def aplr_precisions(sigma: np.ndarray, eps: float) -> np.ndarray:
     return np.array([delta / float(s) for s in sigma], dtype=np.float64)
 
 
-FORMATS = ("afl", "aflp", "bfl", "dfl")
+FORMATS = ("afl", "aflp", "bfl", "dfl", "mp")
+MP_ROUNDOFF = {"mp16": 2.0 ** -11, "mp32": 2.0 ** -24, "mp64": 2.0 ** -53}
 
 
 @dataclass(frozen=True)
@@ -157,6 +164,8 @@ def encode(a: np.ndarray, u: float, fmt: str = "afl") -> AFLUnit:
         return encode_bfl(a, u)
     if fmt == "dfl":
         return encode_dfl(a, u)
+    if fmt == "mp":
+        return encode_mp(a, u)
     if fmt != "afl":
         raise ValueError(f"unknown format {fmt!r}")
     code, m_min, e, m = codes_of(a, u)
@@ -217,10 +226,38 @@ def encode_dfl(a: np.ndarray, u: float) -> AFLUnit:
     return AFLUnit(n=code.size, m_min=1.0, e=11, m=mp, data=pack(code, 12 + mp), fmt="dfl")
 
 
+def mp_format(u: float) -> str:
+    """The cheapest IEEE format (mp16, mp32, mp64) whose unit roundoff is <= u."""
+    for f in ("mp16", "mp32", "mp64"):
+        if MP_ROUNDOFF[f] <= u:
+            return f
+    return "mp64"
+
+
+def encode_mp(a: np.ndarray, u: float, fmt: str | None = None) -> AFLUnit:
+    """MP-D-S-H unit: the values cast (round to nearest even) to the format chosen for u
+    (or to fmt), stored as their IEEE bit patterns."""
+    a = np.ascontiguousarray(a, dtype=np.float64).ravel()
+    f = fmt or mp_format(u)
+    dt, ut, e, m = {"mp16": (np.float16, np.uint16, 5, 10), "mp32": (np.float32, np.uint32, 8, 23),
+                    "mp64": (np.float64, np.uint64, 11, 52)}[f]
+    x = a.astype(dt)
+    if not np.all(np.isfinite(x)):
+        raise ValueError(f"value not finite in {f}")
+    code = x.view(ut).astype(np.uint64)
+    return AFLUnit(n=code.size, m_min=1.0, e=e, m=m, data=pack(code, 1 + e + m), fmt=f)
+
+
 def decode(unit: AFLUnit) -> np.ndarray:
     """Decode a unit to FP64. AFL/AFLP: a = (v - 1) * m_min, negated for a set sign bit;
     BFL: the code shifted back into an FP32 pattern; DFL: into an FP64 pattern."""
     code = unpack(unit.data, unit.n, unit.w)
+    if unit.fmt == "mp16":
+        return code.astype(np.uint16).view(np.float16).astype(np.float64)
+    if unit.fmt == "mp32":
+        return code.astype(np.uint32).view(np.float32).astype(np.float64)
+    if unit.fmt == "mp64":
+        return code.view(np.float64).copy()
     if unit.fmt == "bfl":
         return (code << np.uint64(23 - unit.m)).astype(np.uint32).view(np.float32).astype(np.float64)
     if unit.fmt == "dfl":

@@ -284,7 +284,8 @@ class CHMatrix:
 def compress(H: HMatrix, eps: float | None = None, precision_override: float | None = None,
              fmt: str = "afl") -> CHMatrix:
     """AFL (dense) / AFL-APLR (lowrank) compression of every leaf; fmt selects AFL or one of
-    its byte-aligned variants AFLP, BFL, DFL (Section 3.2), with the same precisions.
+    its byte-aligned variants AFLP, BFL, DFL (Section 3.2), with the same precisions, or the
+    mixed precision comparison format MP-D-S-H ("mp", Section 3.3).
 
     ``precision_override`` replaces every precision (tests use 2^-60 to make m = 52).
     """
@@ -293,7 +294,10 @@ def compress(H: HMatrix, eps: float | None = None, precision_override: float | N
     for b in H.blocks:
         if b.kind == DENSE:
             u = eps if precision_override is None else precision_override
-            units = [afl.encode(b.D.ravel(order="F"), u, fmt)]
+            if fmt == "mp":   # the mixed precision comparison keeps dense leaves in FP64
+                units = [afl.encode_mp(b.D.ravel(order="F"), u, "mp64")]
+            else:
+                units = [afl.encode(b.D.ravel(order="F"), u, fmt)]
             out.append(CBlock(b.row0, b.nrows, b.col0, b.ncols, DENSE, None, units))
         else:
             us = afl.aplr_precisions(b.S, eps)

@@ -84,3 +84,36 @@ def test_compressed_matrix_error(fmt, exp2d_case):
     # byte-aligned formats keep at least the AFL precision of every unit
     assert np.linalg.norm(Af - A, 2) <= 2 * np.linalg.norm(ohm.to_dense(C) - A, 2) + 1e-12 * np.linalg.norm(A, 2)
     assert all(u.fmt == fmt for b in Cf.blocks for u in b.units)
+
+
+def test_mp_units_are_ieee_casts_and_formats_follow_precision():
+    """MP-D-S-H (Section 3.3): each column in the cheapest of FP16/FP32/FP64 whose unit roundoff
+    (Table 1) is <= its precision; the stored values are the round-to-nearest casts."""
+    a = _vals(8) * 1e-3
+    for u, f, dt in ((1e-3, "mp16", np.float16), (2.0 ** -11, "mp16", np.float16), (1e-4, "mp32", np.float32),
+                     (2.0 ** -24, "mp32", np.float32), (1e-8, "mp64", np.float64)):
+        x = np.clip(a, -6e4, 6e4)
+        unit = afl.encode(x, u, "mp")
+        assert unit.fmt == f and unit.w == {"mp16": 16, "mp32": 32, "mp64": 64}[f]
+        assert np.array_equal(afl.decode(unit), x.astype(dt).astype(np.float64))
+
+
+def test_mp_block_error_bound(exp2d_case):
+    """The bound of [AmeBoiBut:2022, Thm 2.1] as quoted in Section 3.3 with p = 3 formats:
+    ||M - W Sigma X^T|| <= (2p - 1 + sum_i sqrt(r_i) u_i) delta per lowrank block; dense leaves exact."""
+    p, H, C = exp2d_case
+    Cm = ohm.compress(H, fmt="mp")
+    for b, cb in zip(H.blocks, Cm.blocks):
+        if b.kind == ohm.DENSE:
+            assert np.array_equal(ohm.decode_block(cb), b.D)
+            continue
+        if not b.rank:
+            continue
+        W, S, X = ohm.decode_block(cb)
+        M = (b.W * b.S) @ b.X.T
+        err = np.linalg.norm(M - (W * S) @ X.T, 2)
+        delta = H.eps * b.S[0]
+        fm = [u.fmt for u in cb.units[:b.rank]]
+        r = {f: fm.count(f) for f in ("mp16", "mp32", "mp64")}
+        bound = (2 * 3 - 1 + sum(np.sqrt(r[f]) * afl.MP_ROUNDOFF[f] for f in r)) * delta
+        assert err <= bound, (err, bound)
