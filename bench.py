@@ -388,7 +388,7 @@ def run_ours(args, world: int, rank: int, local: int):
             del X, Y
         A.check()
         formats = {}
-        for fmt in ("aflp", "bfl", "dfl"):
+        for fmt in ("aflp", "bfl", "dfl", "mp"):
             Af = Hh.upload(fmt)
             inf_f = Af.info
 
@@ -404,7 +404,28 @@ def run_ours(args, world: int, rank: int, local: int):
                             "compressed_bytes": comp, "ratio": comp / inf_f["fp64_bytes"],
                             "speedup_vs_afl": t32 / tf}
             Af.free()
+        # GPU encoder (hlr_encode_device) over every unit of the matrix, against the build time
+        # (the paper reports compression time relative to construction, Section 5.3)
+        vals, off, prec = Hh.unit_arrays("afl")
+        v_d = torch.from_numpy(vals).to(dev)
+        o_d = torch.from_numpy(off).to(dev)
+        u_d = torch.from_numpy(prec).to(dev)
+        del vals
+        enc = hg.encode_device(v_d, o_d, u_d, "afl", stream=stream)
+        torch.cuda.synchronize()
+        out_bytes = int(enc[3][-1].item())
+        rejected = int((enc[1] < 0).sum().item())
+        del enc
+        ke = 5
+        te = time_loop(lambda: hg.encode_device(v_d, o_d, u_d, "afl", stream=stream), ke, stream) / ke
+        in_bytes = v_d.numel() * 8
+        encode = {"ms": te * 1e3, "units": int(u_d.numel()), "input_bytes": in_bytes, "output_bytes": out_bytes,
+                  "input_GB/s": in_bytes / te / 1e9, "hbm_GB/s_algorithmic": (in_bytes + out_bytes) / te / 1e9,
+                  "rejected_units": rejected, "vs_build_time": te / t_build}
+        del v_d, o_d, u_d
+        torch.cuda.empty_cache()
         extra = {
+            "encode_device": encode,
             "formats": formats,
             "multi_rhs": multi,
             "afl_fp64_acc": {"ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9},

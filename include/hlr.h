@@ -49,6 +49,11 @@ extern "C" {
 #define HLR_FMT_AFLP     3  /* AFL with m raised to the smallest m' making 1 + e + m' a multiple of 8 */
 #define HLR_FMT_BFL      4  /* FP32 layout: FP32 cast, mantissa rounded to m' in {7, 15, 23}      */
 #define HLR_FMT_DFL      5  /* FP64 layout: mantissa rounded to m' in {4, 12, ..., 52}             */
+/* Mixed precision comparison format MP-D-S-H (Section 3.3): every lowrank column i is cast
+ * (round to nearest even) to the cheapest of FP16, FP32, FP64 whose unit roundoff (2^-11,
+ * 2^-24, 2^-53; Table 1) is <= its precision eps sigma_0 / sigma_i; dense leaves stay FP64.
+ * Values beyond the chosen format's range are rejected (HLR_ERR_INVALID). */
+#define HLR_FMT_MP       6
 
 /* ---- product flags ---------------------------------------------------------------------- */
 #define HLR_ACC_FP64 0  /* decode to FP64 and accumulate in FP64 everywhere                    */
@@ -87,7 +92,7 @@ typedef struct {
   int64_t nblocks;
   const hlr_block_desc *blocks;
   double eps;
-  int32_t format;   /* HLR_FMT_AFL_APLR, HLR_FMT_AFLP, HLR_FMT_BFL, HLR_FMT_DFL or HLR_FMT_FP64 */
+  int32_t format;   /* HLR_FMT_AFL_APLR, _AFLP, _BFL, _DFL, _MP or HLR_FMT_FP64 */
   int32_t tuning;   /* 0: default work layout; else HLR_TUNING(sub, leaf, piece_kb), AFL only */
 } hlr_hmatrix_desc;
 
@@ -200,11 +205,36 @@ int hlr_afl_encode(const double *a, int64_t n, double u, double *m_min, int32_t 
                    uint8_t *out, size_t cap, size_t *nbytes);
 
 /* hlr_afl_encode for any compressed format (HLR_FMT_AFL_APLR, HLR_FMT_AFLP, HLR_FMT_BFL,
- * HLR_FMT_DFL), Section 3.2: same arguments and errors; for BFL and DFL *m_min is 1 and *e the
- * fixed exponent width (8, 11). BFL also fails (HLR_ERR_INVALID) for values that are not finite
- * in FP32 after the cast and rounding. */
+ * HLR_FMT_DFL, HLR_FMT_MP), Sections 3.2 and 3.3: same arguments and errors; for BFL, DFL and
+ * MP *m_min is 1 and *e the exponent width of the layout (BFL 8, DFL 11; MP 5, 8 or 11 for the
+ * FP16, FP32 or FP64 the precision u selects, *m then 10, 23 or 52). BFL and MP also fail
+ * (HLR_ERR_INVALID) for values that are not finite after the cast and rounding. */
 int hlr_encode(int32_t format, const double *a, int64_t n, double u, double *m_min, int32_t *e, int32_t *m,
                uint8_t *out, size_t cap, size_t *nbytes);
+
+/* Encode nunits units on the GPU in format fmt (any compressed format; Section 3.2, and
+ * Section 3.3 for the per-column precisions of AFL-APLR and the MP layout), writing for every
+ * unit the very bytes hlr_encode writes for it. This is the device side of compressing data
+ * where it is built (Section 5.3: compression as part of the construction).
+ *   off_dev[nunits + 1] (device, int64): unit u is a_dev[off_dev[u] .. off_dev[u+1]);
+ *   total_values       (host): off_dev[nunits], used to check cap;
+ *   a_dev (device, FP64), u_dev[nunits] (device, FP64): the values and each unit's precision
+ *     (dense leaf: eps, or for MP any u < 2^-53, i.e. FP64; column i of a lowrank block:
+ *     eps sigma_0 / sigma_i);
+ *   m_min_dev, e_dev, m_dev [nunits] (device, out): the unit parameters as hlr_encode returns
+ *     them; e_dev[u] = -1 marks a rejected unit, which gets no stream: one hlr_encode would
+ *     reject (NaN / Inf, a value beyond the format's range, a precision that is not positive
+ *     and finite) or one whose offsets decrease or leave [0, total_values] (its values are
+ *     then not read);
+ *   out_off_dev[nunits + 1] (device, out): unit u's stream is out_dev[out_off_dev[u] ..
+ *     out_off_dev[u+1]) (each padded to 16 bytes; out_off_dev[nunits] = total bytes);
+ *   out_dev (device, 16-byte aligned, cap bytes >= 8 total_values + 16 nunits).
+ * Asynchronous on cuda_stream (three kernels, no allocation, no synchronisation); capturable
+ * into a CUDA graph. Errors: HLR_ERR_INVALID (format, null or misaligned pointers, negative
+ * sizes), HLR_ERR_OOM (cap below the bound), HLR_ERR_CUDA (launch). */
+int hlr_encode_device(int32_t fmt, int64_t nunits, const int64_t *off_dev, int64_t total_values, const double *a_dev,
+                      const double *u_dev, double *m_min_dev, int32_t *e_dev, int32_t *m_dev, int64_t *out_off_dev,
+                      uint8_t *out_dev, size_t cap, void *cuda_stream);
 
 /* Decode one AFL stream on the GPU into n FP64 values, bit-exact IEEE round-to-nearest
  * ((v - 1) * m_min without contraction, Section 3.2). stream_dev must be 16-byte aligned and

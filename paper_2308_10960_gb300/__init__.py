@@ -25,8 +25,9 @@ __all__ = [
 
 _ACC = {"fp32": HLR_ACC_FP32, "fp64": HLR_ACC_FP64, HLR_ACC_FP32: HLR_ACC_FP32, HLR_ACC_FP64: HLR_ACC_FP64}
 _FMT = {"afl": HLR_FMT_AFL_APLR, "fp64": HLR_FMT_FP64, "aflp": B.HLR_FMT_AFLP, "bfl": B.HLR_FMT_BFL,
-        "dfl": B.HLR_FMT_DFL, HLR_FMT_AFL_APLR: HLR_FMT_AFL_APLR, HLR_FMT_FP64: HLR_FMT_FP64,
-        B.HLR_FMT_AFLP: B.HLR_FMT_AFLP, B.HLR_FMT_BFL: B.HLR_FMT_BFL, B.HLR_FMT_DFL: B.HLR_FMT_DFL}
+        "dfl": B.HLR_FMT_DFL, "mp": B.HLR_FMT_MP, HLR_FMT_AFL_APLR: HLR_FMT_AFL_APLR, HLR_FMT_FP64: HLR_FMT_FP64,
+        B.HLR_FMT_AFLP: B.HLR_FMT_AFLP, B.HLR_FMT_BFL: B.HLR_FMT_BFL, B.HLR_FMT_DFL: B.HLR_FMT_DFL,
+        B.HLR_FMT_MP: B.HLR_FMT_MP}
 _KERNEL = {"exp2d": HLR_KERNEL_EXP, "exp": HLR_KERNEL_EXP, "laplace": HLR_KERNEL_LAPLACE,
            "matern15": HLR_KERNEL_MATERN15}
 
@@ -46,10 +47,11 @@ def _stream_ptr(stream) -> int | None:
     return stream.cuda_stream
 
 
-def _dev_ptr(t, n: int | None = None) -> int:
+def _dev_ptr(t, n: int | None = None, dtype=None) -> int:
     import torch
-    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-        raise HlrError(HLR_ERR_INVALID, "expected a contiguous float64 CUDA tensor")
+    dtype = torch.float64 if dtype is None else dtype
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise HlrError(HLR_ERR_INVALID, f"expected a contiguous {dtype} CUDA tensor")
     if n is not None and t.numel() < n:
         raise HlrError(HLR_ERR_INVALID, f"tensor has {t.numel()} elements, need {n}")
     return t.data_ptr()
@@ -259,6 +261,21 @@ class HostHMatrix:
                 if k else np.zeros((d.ncols, 0))
         return b
 
+    def unit_arrays(self, fmt: str = "afl", eps: float | None = None):
+        """The matrix's units in upload order as (values, offsets, precisions): see
+        ``unit_arrays``; reads the blocks in place (no per-block copies)."""
+        def views():
+            for i in range(self.desc.nblocks):
+                d = self.desc.blocks[i]
+                if d.kind == HLR_DENSE:
+                    yield {"kind": d.kind, "D": np.ctypeslib.as_array(d.D, shape=(d.nrows * d.ncols,))}
+                elif d.rank > 0:
+                    k = d.rank
+                    yield {"kind": d.kind, "S": np.ctypeslib.as_array(d.sigma, shape=(k,)),
+                           "W": np.ctypeslib.as_array(d.W, shape=(d.nrows * k,)).reshape(d.nrows, k, order="F"),
+                           "X": np.ctypeslib.as_array(d.X, shape=(d.ncols * k,)).reshape(d.ncols, k, order="F")}
+        return unit_arrays(views(), self.eps if eps is None else float(eps), fmt)
+
     def upload(self, fmt="afl", eps: float | None = None, stream=None, tuning: int = 0) -> DeviceHMatrix:
         """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU. tuning:
         work layout of the AFL kernels (``tuning_code``; 0 = default)."""
@@ -304,7 +321,7 @@ def build_kernel_hmatrix(points: np.ndarray, kernel: str, eps: float, scale: flo
 
 
 def encode(a: np.ndarray, u: float, fmt: str = "afl"):
-    """Host encoder of the library for any compressed format (afl, aflp, bfl, dfl): returns
+    """Host encoder of the library for any compressed format (afl, aflp, bfl, dfl, mp): returns
     (m_min, e, m, stream bytes padded to 16)."""
     a = np.ascontiguousarray(a, dtype=np.float64).ravel()
     m_min = C.c_double(0)
@@ -317,6 +334,61 @@ def encode(a: np.ndarray, u: float, fmt: str = "afl"):
     B.check(B.lib.hlr_encode(f, B.f64ptr(a), a.size, float(u), C.byref(m_min), C.byref(e), C.byref(m),
                              buf.ctypes.data, cap, C.byref(nbytes)))
     return m_min.value, e.value, m.value, buf[: nbytes.value].tobytes()
+
+
+def encode_device(values, offsets, precisions, fmt: str = "afl", stream=None):
+    """GPU encoder of the library (hlr_encode_device): units values[offsets[u]:offsets[u+1]]
+    (FP64 / int64 CUDA tensors) at precisions[u], encoded on the device in one asynchronous
+    call. Returns (m_min, e, m, out_off, out) as CUDA tensors; unit u's stream, byte for byte
+    what encode() writes, is out[out_off[u]:out_off[u+1]]; e[u] = -1 marks a rejected unit."""
+    import torch
+    nunits = precisions.numel()
+    total = values.numel()
+    dev = values.device
+    m_min = torch.empty(nunits, dtype=torch.float64, device=dev)
+    e = torch.empty(nunits, dtype=torch.int32, device=dev)
+    m = torch.empty(nunits, dtype=torch.int32, device=dev)
+    out_off = torch.empty(nunits + 1, dtype=torch.int64, device=dev)
+    cap = 8 * total + 16 * nunits + 16
+    out = torch.empty(cap, dtype=torch.uint8, device=dev)
+    f = _FMT[fmt] if fmt in _FMT else int(fmt)
+    if offsets.numel() != nunits + 1:
+        raise HlrError(HLR_ERR_INVALID, "offsets must hold nunits + 1 entries")
+    B.check(B.lib.hlr_encode_device(f, nunits, _dev_ptr(offsets, dtype=torch.int64), total, _dev_ptr(values),
+                                    _dev_ptr(precisions), _dev_ptr(m_min), _dev_ptr(e, dtype=torch.int32),
+                                    _dev_ptr(m, dtype=torch.int32), _dev_ptr(out_off, dtype=torch.int64),
+                                    _dev_ptr(out, dtype=torch.uint8), cap, _stream_ptr(stream)))
+    return m_min, e, m, out_off, out
+
+
+def unit_arrays(blocks, eps: float, fmt: str = "afl"):
+    """Host: the units of a block list in upload order (dense leaf: its column-major values;
+    lowrank block: W columns, then X columns) as (values, offsets, precisions) numpy arrays,
+    with the precisions upload gives them (dense eps, lowrank column i eps sigma_0 / sigma_i;
+    MP dense leaves 2^-60, i.e. FP64)."""
+    vals, lens, prec = [], [], []
+    for b in blocks:
+        if b["kind"] == HLR_DENSE:
+            D = np.asarray(b["D"], dtype=np.float64)
+            vals.append(D.ravel(order="F") if D.ndim == 2 else D)
+            lens.append(D.size)
+            prec.append(2.0 ** -60 if fmt == "mp" else eps)
+        else:
+            S = np.asarray(b["S"], dtype=np.float64)
+            k = S.size
+            if k == 0:
+                continue
+            W = np.asarray(b["W"], dtype=np.float64)
+            X = np.asarray(b["X"], dtype=np.float64)
+            u = (eps * S[0]) / S
+            vals += [W.ravel(order="F"), X.ravel(order="F")]
+            lens += [W.shape[0]] * k + [X.shape[0]] * k
+            prec += [u, u]
+    off = np.zeros(len(lens) + 1, dtype=np.int64)
+    np.cumsum(lens, out=off[1:])
+    v = np.concatenate(vals) if vals else np.zeros(0)
+    pr = np.concatenate([np.atleast_1d(np.asarray(q, dtype=np.float64)) for q in prec]) if prec else np.zeros(0)
+    return v, off, pr
 
 
 def afl_encode(a: np.ndarray, u: float):

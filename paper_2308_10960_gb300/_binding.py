@@ -29,6 +29,7 @@ HLR_FMT_FP64 = 2
 HLR_FMT_AFLP = 3
 HLR_FMT_BFL = 4
 HLR_FMT_DFL = 5
+HLR_FMT_MP = 6
 HLR_ACC_FP64 = 0
 HLR_ACC_FP32 = 1
 HLR_PROFILE = 0x100
@@ -94,6 +95,8 @@ SIGNATURES = [
                                  C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
     ("hlr_encode", C.c_int, [C.c_int32, _dp, C.c_int64, C.c_double, _dp, C.POINTER(C.c_int32),
                              C.POINTER(C.c_int32), C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    ("hlr_encode_device", C.c_int, [C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("hlr_afl_decode_device", C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_int32, C.c_int32, C.c_void_p,
                                         C.c_void_p]),
     ("hlr_decode_units", C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),

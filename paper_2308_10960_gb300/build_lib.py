@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhlr_gb300.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU = ["hlr_kernels.cu", "hlr_cg.cu"]
+CU = ["hlr_kernels.cu", "hlr_cg.cu", "hlr_encode.cu"]
 CPP = ["hlr_codec.cpp", "hlr_upload.cpp", "hlr_pack.cpp", "hlr_build.cpp"]
 
 

@@ -12,6 +12,8 @@
 // 1 + 8 + m' bits of the FP32 pattern of the value (cast to nearest, then rounded half up to
 // m' in {7, 15, 23}); DFL the top 1 + 11 + m' bits of the FP64 pattern rounded half up to
 // m' in {4, 12, ..., 52}.
+// MP (Section 3.3) stores each unit as IEEE FP16, FP32 or FP64 bit patterns (round to nearest
+// even), the cheapest of the three whose unit roundoff 2^-11, 2^-24, 2^-53 is <= u.
 // Compiled with -ffp-contract=off: every FP64 operation is a separately rounded IEEE op.
 #include <cmath>
 #include <cstring>
@@ -113,7 +115,49 @@ static inline uint32_t fbits(float x) {
   return b;
 }
 
+// x rounded to nearest even into an IEEE binary16 pattern; false if it overflows. The
+// quantum of the result is 2^(max(E, -14) - 10) for x = f 2^E, f in [1, 2) (2^-24 for the
+// subnormal range): x / quantum rounded to an integer q is the significand with the implicit
+// bit, and (E + 15) << 10 plus q - 1024 the pattern (a carry of q to 2048 moves into the
+// exponent; below 2^-14 the pattern is q itself).
+static bool half_bits(double x, uint16_t *out) {
+  if (!std::isfinite(x)) return false;
+  const double ax = std::fabs(x);
+  int E = 0;
+  std::frexp(ax, &E);
+  const int ue = ax == 0.0 ? -25 : E - 1;
+  const int qe = (ue < -14 ? -14 : ue) - 10;
+  const double q = std::nearbyint(std::ldexp(ax, -qe));  // exact scaling, ties to even
+  uint64_t code;
+  if (ue < -14) {
+    code = uint64_t(q);
+  } else {
+    code = (uint64_t(ue + 15) << 10) + uint64_t(q) - 1024;
+    if (code >= 0x7C00) return false;
+  }
+  if (x < 0.0 || (x == 0.0 && std::signbit(x))) code |= 0x8000;
+  *out = uint16_t(code);
+  return true;
+}
+
+static int mp_kind(double u) { return u >= 0x1p-11 ? 16 : u >= 0x1p-24 ? 32 : 64; }
+
 bool unit_params(int fmt, const double *a, int64_t n, double u, AflParams *p) {
+  if (fmt == HLR_FMT_MP) {
+    const int bits = mp_kind(u);
+    for (int64_t j = 0; j < n; ++j) {
+      uint16_t h;
+      if (bits == 16 && !half_bits(a[j], &h)) return false;
+      if (bits == 32 && !std::isfinite(float(a[j]))) return false;
+      if (!std::isfinite(a[j])) return false;
+    }
+    p->kind = VF_MP;
+    p->m_min = 1.0;
+    p->e = bits == 16 ? 5 : bits == 32 ? 8 : 11;
+    p->m = bits == 16 ? 10 : bits == 32 ? 23 : 52;
+    p->w = bits;
+    return true;
+  }
   const int m = mantissa_bits(u);
   if (fmt == HLR_FMT_AFL_APLR) return afl_params_m(a, n, m, p);
   if (fmt == HLR_FMT_AFLP) {
@@ -164,7 +208,11 @@ void unit_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out) {
   const int w = p.w;
   for (int64_t j = 0; j < n; ++j) {
     uint64_t code;
-    if (p.kind == VF_BFL) {
+    if (p.kind == VF_MP) {
+      uint16_t h = 0;
+      if (w == 16) half_bits(a[j], &h);
+      code = w == 16 ? uint64_t(h) : w == 32 ? uint64_t(fbits(float(a[j]))) : dbits(a[j]);
+    } else if (p.kind == VF_BFL) {
       uint64_t b = fbits(float(a[j]));
       if (p.m < 23) b = (b + (uint64_t(1) << (22 - p.m))) & ~((uint64_t(1) << (23 - p.m)) - 1);
       code = b >> (23 - p.m);
@@ -188,7 +236,8 @@ extern "C" int hlr_encode(int32_t fmt, const double *a, int64_t n, double u, dou
     return set_error(HLR_ERR_INVALID, "hlr_encode: null argument or negative n");
   if (!(u > 0.0) || !std::isfinite(u))
     return set_error(HLR_ERR_INVALID, "hlr_encode: precision must be positive and finite");
-  if (fmt != HLR_FMT_AFL_APLR && fmt != HLR_FMT_AFLP && fmt != HLR_FMT_BFL && fmt != HLR_FMT_DFL)
+  if (fmt != HLR_FMT_AFL_APLR && fmt != HLR_FMT_AFLP && fmt != HLR_FMT_BFL && fmt != HLR_FMT_DFL &&
+      fmt != HLR_FMT_MP)
     return set_error(HLR_ERR_INVALID, "hlr_encode: unknown format");
   AflParams p;
   if (!unit_params(fmt, a, n, u, &p)) return set_error(HLR_ERR_INVALID, "hlr_encode: value not representable");

@@ -37,7 +37,9 @@ constexpr int kSubRows = 64;      // phase 1: rows of an X column read by one la
 constexpr int kLeafRows = 64;
 
 enum : uint8_t { SEG_DENSE = 0, SEG_W = 1, SEG_X = 2 };
-enum { VF_AFL = 0, VF_BFL = 1, VF_DFL = 2 };  // value formats of the stored codes
+// value formats of the stored codes; VF_MP: IEEE FP16 / FP32 / FP64 patterns, the lane's e
+// (5, 8, 11) telling which
+enum { VF_AFL = 0, VF_BFL = 1, VF_DFL = 2, VF_MP = 3 };
 enum : uint8_t { PF_START_LEAF = 1, PF_END_LEAF = 2 };
 
 struct PieceHdr {
@@ -166,7 +168,7 @@ struct DevLayout {
   double *ydev;              // [n]
   int64_t n;
   int32_t ncnt, raw;         // raw = 1 for HLR_FMT_FP64
-  int32_t vfmt, pad;         // value format of the codes: VF_AFL (AFL, AFLP), VF_BFL, VF_DFL
+  int32_t vfmt, pad;         // value format of the codes: VF_AFL (AFL, AFLP), VF_BFL, VF_DFL, VF_MP
 };
 
 struct Handle {
@@ -213,12 +215,13 @@ int mantissa_bits(double u);
 struct AflParams {
   double m_min;
   int e, m, w;
-  int kind;  // value format of the codes: VF_AFL (AFL, AFLP), VF_BFL, VF_DFL
+  int kind;  // value format of the codes: VF_AFL (AFL, AFLP), VF_BFL, VF_DFL, VF_MP
 };
 bool afl_params(const double *a, int64_t n, double u, AflParams *p);
 void afl_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out);
-// Parameters and codes of one unit in format fmt (HLR_FMT_AFL_APLR, _AFLP, _BFL, _DFL); false
-// for non-finite input (or values that overflow the BFL / DFL layout).
+// Parameters and codes of one unit in format fmt (HLR_FMT_AFL_APLR, _AFLP, _BFL, _DFL, _MP);
+// false for non-finite input (or values that overflow the BFL / DFL / MP layout). MP with
+// u = 0 selects FP64.
 bool unit_params(int fmt, const double *a, int64_t n, double u, AflParams *p);
 void unit_pack(const double *a, int64_t n, const AflParams &p, uint8_t *out);
 inline size_t padded16(size_t b) { return (b + 15) & ~size_t(15); }

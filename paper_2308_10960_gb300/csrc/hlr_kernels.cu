@@ -26,6 +26,7 @@
 //            over the <= 32 slices of a warp (phase 2); compensated FP32 pairs across pieces;
 //            FP64 for the final per-row sum into y.
 // FMT_AFL64: codes -> FP64, FP64 sums.   FMT_RAW64: plain FP64 factors (uncompressed baseline).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -38,11 +39,11 @@
 namespace hlr {
 
 // Kernel formats: the stored values (AFL family, BFL, DFL, plain FP64) and the accumulation.
-enum { FMT_AFL32 = 0, FMT_AFL64 = 1, FMT_RAW64 = 2, FMT_BFL32 = 3, FMT_DFL32 = 4 };
+enum { FMT_AFL32 = 0, FMT_AFL64 = 1, FMT_RAW64 = 2, FMT_BFL32 = 3, FMT_DFL32 = 4, FMT_MP32 = 5 };
 template <int FMT>
-constexpr bool kFP32 = FMT == FMT_AFL32 || FMT == FMT_BFL32 || FMT == FMT_DFL32;
+constexpr bool kFP32 = FMT == FMT_AFL32 || FMT == FMT_BFL32 || FMT == FMT_DFL32 || FMT == FMT_MP32;
 template <int FMT>
-constexpr int kVF = FMT == FMT_BFL32 ? VF_BFL : FMT == FMT_DFL32 ? VF_DFL : VF_AFL;
+constexpr int kVF = FMT == FMT_BFL32 ? VF_BFL : FMT == FMT_DFL32 ? VF_DFL : FMT == FMT_MP32 ? VF_MP : VF_AFL;
 constexpr int kThreads = kConsumers + 32;
 constexpr int kCWarps = kConsumers / 32;
 constexpr unsigned kFull = 0xffffffffu;
@@ -62,6 +63,8 @@ template <>
 struct Tr<FMT_BFL32> : Tr<FMT_AFL32> {};
 template <>
 struct Tr<FMT_DFL32> : Tr<FMT_AFL32> {};
+template <>
+struct Tr<FMT_MP32> : Tr<FMT_AFL32> {};
 constexpr int kRB = 8;          // right-hand sides per pass of the multi-RHS product
 constexpr int kMaxBatch = 64;   // products per launch of the batched path
 
@@ -227,11 +230,21 @@ __device__ __forceinline__ float dec_dfl32(uint32_t code, const ColDec &c) {
   const uint32_t x = code << (20 - c.m);
   return __uint_as_float((((x & 0x7fffffffu) - 0x38000000u) << 3) | (x & 0x80000000u));
 }
+// MP codes (Section 3.3): IEEE patterns, FP16 (e = 5) widened by the hardware conversion, FP32
+// (e = 8) as they are; the bits above a 16-bit code are dropped
+__device__ __forceinline__ float dec_mp32(uint32_t code, const ColDec &c) {
+  return c.e == 5 ? __half2float(__ushort_as_half(static_cast<unsigned short>(code & 0xffffu))) : __uint_as_float(code);
+}
+__device__ __forceinline__ double dec_mp64(uint64_t code, const ColDec &c) {
+  if (c.e == 11) return __longlong_as_double(static_cast<long long>(code));
+  return double(dec_mp32(uint32_t(code), c));
+}
 // value of a code of any width and value format in FP64: AFL family +-(v - 1) (to be scaled by
-// m_min), BFL and DFL the stored value itself
+// m_min), BFL, DFL and MP the stored value itself
 __device__ __forceinline__ double dec_any64(uint64_t code, const ColDec &c, int vf) {
   if (vf == VF_BFL) return double(__uint_as_float(uint32_t(code << (23 - c.m))));
   if (vf == VF_DFL) return __longlong_as_double(static_cast<long long>(code << (52 - c.m)));
+  if (vf == VF_MP) return dec_mp64(code, c);
   return dec_f64(code, c);
 }
 // FP32 family: the value entering the phase-1 dot product, and value times multiplier
@@ -241,6 +254,8 @@ __device__ __forceinline__ float val32(uint32_t code, const ColDec &c) {
     return dec_bfl(code, c);
   else if constexpr (FMT == FMT_DFL32)
     return dec_dfl32(code, c);
+  else if constexpr (FMT == FMT_MP32)
+    return dec_mp32(code, c);
   else
     return dec_f32(code, c);
 }
@@ -256,6 +271,8 @@ template <int FMT>
 __device__ __forceinline__ bool fast_dec(const ColDec &c) {
   if constexpr (FMT == FMT_BFL32)
     return true;
+  else if constexpr (FMT == FMT_MP32)
+    return c.narrow;  // FP16 and FP32 columns (FP64 ones take the 64-bit window)
   else
     return c.fast32;  // DFL: set by lane_dec for marked slices
 }
@@ -1272,6 +1289,11 @@ __device__ double decode_exact_vf(uint64_t code, int e, int m, double m_min, int
   if (w < 64) code &= (1ull << w) - 1ull;
   if (vf == VF_BFL) return double(__uint_as_float(uint32_t(code << (23 - m))));
   if (vf == VF_DFL) return __longlong_as_double(static_cast<long long>(code << (52 - m)));
+  if (vf == VF_MP) {
+    if (e == 5) return double(__half2float(__ushort_as_half(static_cast<unsigned short>(code))));
+    if (e == 8) return double(__uint_as_float(uint32_t(code)));
+    return __longlong_as_double(static_cast<long long>(code));
+  }
   return decode_code_exact(code, e, m, m_min);
 }
 
@@ -1340,6 +1362,8 @@ void set_smem_attrs() {
   set_smem_attr<FMT_BFL32, 1, 1, NB>();
   set_smem_attr<FMT_DFL32, 0, 1, NB>();
   set_smem_attr<FMT_DFL32, 1, 1, NB>();
+  set_smem_attr<FMT_MP32, 0, 1, NB>();
+  set_smem_attr<FMT_MP32, 1, 1, NB>();
 }
 
 const DevProps &props(int dev) {
@@ -1453,6 +1477,8 @@ int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream
     launch_jobs<FMT_BFL32, 1, 1>(J, st, ev);
   else if (H.L.vfmt == VF_DFL)
     launch_jobs<FMT_DFL32, 1, 1>(J, st, ev);
+  else if (H.L.vfmt == VF_MP)
+    launch_jobs<FMT_MP32, 1, 1>(J, st, ev);
   else
     launch_jobs<FMT_AFL32, 1, 1>(J, st, ev);
   return cuda_status("hlr_matvec: launch");
@@ -1528,6 +1554,7 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   Batcher<FMT_AFL32, 1> b32(st);
   Batcher<FMT_BFL32, 1> bbfl(st);
   Batcher<FMT_DFL32, 1> bdfl(st);
+  Batcher<FMT_MP32, 1> bmp(st);
   Batcher<FMT_AFL64, 1> b64(st);
   Batcher<FMT_RAW64, 1> braw(st);
   Batcher<FMT_AFL32, kRB> bm(st);  // multi-column passes decode the AFL family only
@@ -1573,6 +1600,8 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
           bbfl.add(&Hq, -1, jb);
         else if (Hq.L.vfmt == VF_DFL)
           bdfl.add(&Hq, -1, jb);
+        else if (Hq.L.vfmt == VF_MP)
+          bmp.add(&Hq, -1, jb);
         else
           b32.add(&Hq, -1, jb);
       }
@@ -1581,6 +1610,7 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   b32.flush();
   bbfl.flush();
   bdfl.flush();
+  bmp.flush();
   b64.flush();
   braw.flush();
   bm.flush();

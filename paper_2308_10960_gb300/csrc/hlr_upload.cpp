@@ -73,7 +73,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   if (n <= 0 || n > (int64_t(1) << 31) - 64) return set_error(HLR_ERR_INVALID, "hlr_upload: n out of range");
   if (d->nblocks <= 0 || !d->blocks) return set_error(HLR_ERR_INVALID, "hlr_upload: no blocks");
   if (d->format != HLR_FMT_AFL_APLR && d->format != HLR_FMT_FP64 && d->format != HLR_FMT_AFLP &&
-      d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL)
+      d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL && d->format != HLR_FMT_MP)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
   int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
   if (d->tuning != 0) {
@@ -173,6 +173,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   in.nblocks = nb;
   std::vector<const double *> usrc;
   std::vector<double> uprec;
+  std::vector<char> rowside;  // dense and W units: their lanes hold a leaf's rows in phase 2
   in.blk_unit0.assign(nb, -1);
   for (int64_t b = 0; b < nb; ++b) {
     const hlr_block_desc &B = d->blocks[b];
@@ -180,7 +181,8 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       in.blk_unit0[b] = int64_t(usrc.size());
       usrc.push_back(B.D);
       in.unit_len.push_back(B.nrows * B.ncols);
-      uprec.push_back(d->eps);
+      uprec.push_back(d->format == HLR_FMT_MP ? 0.0 : d->eps);  // MP keeps dense leaves in FP64
+      rowside.push_back(1);
     } else if (B.rank > 0) {
       in.blk_unit0[b] = int64_t(usrc.size());
       const double delta = d->eps * B.sigma[0];
@@ -188,11 +190,13 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
         usrc.push_back(B.W + i * B.nrows);
         in.unit_len.push_back(B.nrows);
         uprec.push_back(delta / B.sigma[i]);
+        rowside.push_back(1);
       }
       for (int i = 0; i < B.rank; ++i) {
         usrc.push_back(B.X + i * B.ncols);
         in.unit_len.push_back(B.ncols);
         uprec.push_back(delta / B.sigma[i]);
+        rowside.push_back(0);
       }
     }
   }
@@ -210,6 +214,16 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     }
   }
   if (bad) return set_error(HLR_ERR_INVALID, "hlr_upload: NaN or Inf in block data (or beyond the format's range)");
+  // A phase-2 lane holds one column over the task's rows, in a warp region of 32 such lanes:
+  // 64 rows of 64-bit codes (FP64 values of MP, DFL at m' = 52) make a 16 KiB region, more than
+  // a piece holds with its headers, so the default layout then takes tasks of 32 rows.
+  if (afl && d->tuning == 0) {
+    for (int64_t u = 0; u < nunits; ++u)
+      if (rowside[u] && 64 + 128 * ((int64_t(in.prm[u].w) * kLeafRows + 31) / 32) > int64_t(piece_max)) {
+        leaf_rows = kLeafRows / 2;
+        break;
+      }
+  }
   in.uoff.assign(nunits + 1, 0);
   uint64_t stream_bytes = 0;
   for (int64_t u = 0; u < nunits; ++u) {
@@ -386,7 +400,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   L.n = n;
   L.ncnt = int32_t(po.ncnt);
   L.raw = afl ? 0 : 1;
-  L.vfmt = d->format == HLR_FMT_BFL ? VF_BFL : d->format == HLR_FMT_DFL ? VF_DFL : VF_AFL;
+  L.vfmt = d->format == HLR_FMT_BFL ? VF_BFL : d->format == HLR_FMT_DFL ? VF_DFL : d->format == HLR_FMT_MP ? VF_MP : VF_AFL;
   H->nunits = nunits;
   H->values = values;
   H->part_total = po.part_total;

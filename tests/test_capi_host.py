@@ -176,8 +176,64 @@ def test_host_encoder_all_formats_byte_exact(fmt, u):
         assert data == ref.data, (fmt, u)
 
 
+@pytest.mark.parametrize("u", [0.5, 2.0 ** -11, 1e-4, 2.0 ** -24, 1e-9, 0.0])
+def test_host_encoder_mp_byte_exact(u):
+    """MP units (Section 3.3): hlr_encode picks the oracle's IEEE format for u and writes the same
+    round-to-nearest-even patterns, through FP16 subnormals, ties and the largest finite half."""
+    g = np.random.default_rng(22)
+    t = 2.0 ** -11
+    special = np.array([0.0, -0.0, 1.0 + t, 1.0 + 3 * t, -(1.0 + t), 2.0 ** -24, 2.0 ** -25, 3 * 2.0 ** -26,
+                        2.0 ** -14 - 2.0 ** -26, 6.1e-5, 65504.0, 65519.99, -65519.99, 1e-30, 2049.0, 2051.0])
+    for a in (g.standard_normal(333) * np.exp(g.uniform(-20, 9, 333)), special, np.zeros(3)):
+        if u == 0.0:   # the encoder's "FP64" precision: the oracle selects by name
+            ref = afl.encode_mp(a, u, "mp64")
+            mm, e, m, data = hg.encode(a, 2.0 ** -60, "mp")
+        else:
+            ref = afl.encode(a, u, "mp")
+            mm, e, m, data = hg.encode(a, u, "mp")
+        assert (e, m, mm) == (ref.e, ref.m, 1.0) and data == ref.data, u
+
+
+def test_host_encoder_mp_rejects_overflow():
+    with pytest.raises(hg.HlrError):
+        hg.encode(np.array([65520.0]), 0.5, "mp")
+    with pytest.raises(hg.HlrError):
+        hg.encode(np.array([1e39]), 1e-5, "mp")
+    with pytest.raises(ValueError):
+        afl.encode(np.array([65520.0]), 0.5, "mp")
+    assert hg.encode(np.array([1e39]), 1e-9, "mp")[1] == 11
+
+
 def test_host_encoder_rejects_values_outside_bfl():
     with pytest.raises(hg.HlrError):
         hg.encode(np.array([1e300]), 1e-6, "bfl")
     with pytest.raises(hg.HlrError):
         hg.encode(np.array([1.0]), 1e-6, 9)
+
+
+@pytest.mark.parametrize("fmt", ["afl", "mp"])
+def test_unit_arrays_follow_the_oracle_unit_order(fmt, exp2d_case):
+    """unit_arrays lists the units as upload and the oracle's compress do (dense column-major;
+    lowrank W columns then X columns) with the same precisions."""
+    p, H, _ = exp2d_case
+    C = ohm.compress(H, fmt=fmt)
+    vals, off, prec = hg.unit_arrays(oracle_blocks(H), H.eps, fmt)
+    units = [u for cb in C.blocks for u in cb.units]
+    assert len(units) == prec.size == off.size - 1
+    for k in range(0, len(units), 97):
+        a = vals[off[k]:off[k + 1]]
+        assert afl.encode(a, prec[k], fmt).data == units[k].data
+
+
+def test_host_hmatrix_unit_arrays_match_block_copies():
+    p = synth.laplace_problem(2048)
+    Hh = hg.build_kernel_hmatrix(p.points, "laplace", 1e-6, diag=p.params["diag"])
+    try:
+        blocks = [Hh.block(i) for i in range(Hh.structure().shape[0])]
+        for fmt in ("afl", "mp"):
+            a = Hh.unit_arrays(fmt)
+            b = hg.unit_arrays(blocks, Hh.eps, fmt)
+            for x, y in zip(a, b):
+                assert np.array_equal(x, y)
+    finally:
+        Hh.free()
