@@ -650,21 +650,24 @@ __device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const 
 // (in bounds) and are dropped. GEN: the generic FP64 decode (wide codes, large e or m).
 template <bool GEN, int FMT>
 __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t *col, const ColDec &c, float mult) {
+  const uint32_t col_s = smem_u32(col);  // 32-bit shared-memory address of the lane column
+  // chunks of 8 rows: leaves of the cluster tree hold 32..64 rows, so a row count that is not a
+  // multiple of the chunk costs at most 7 predicated decodes
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if (16 * k >= nr) break;
-    if (!GEN && 16 * k + 16 <= nr) {  // a whole chunk of the leaf: no row checks
-      uint32_t bit = uint32_t(16 * k) * c.w;
+  for (int k = 0; k < 8; ++k) {
+    if (8 * k >= nr) break;
+    if (!GEN && 8 * k + 8 <= nr) {  // a whole chunk of the leaf: no row checks
+      uint32_t bit = uint32_t(8 * k) * c.w;
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr, bit += c.w) acc[16 * k + rr] += valmul32<FMT>(bc_code32(col, bit), c, mult);
+      for (int rr = 0; rr < 8; ++rr, bit += c.w) acc[8 * k + rr] += valmul32<FMT>(bc_code32_s(col_s, bit), c, mult);
     } else {
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr) {
-        const int r = 16 * k + rr;
+      for (int rr = 0; rr < 8; ++rr) {
+        const int r = 8 * k + rr;
         const bool ok = r < nr;
         const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
         const float p = GEN ? float(dec_any64(bc_code64(col, bit), c, kVF<FMT>)) * mult
-                            : valmul32<FMT>(bc_code32(col, bit), c, mult);
+                            : valmul32<FMT>(bc_code32_s(col_s, bit), c, mult);
         if (ok) acc[r] += p;
       }
     }
