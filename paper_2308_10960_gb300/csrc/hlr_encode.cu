@@ -4,17 +4,22 @@
 // instead of being copied to the host first (the paper's advice to compress during
 // construction, Section 5.3).
 //
-// Three launches on the caller's stream, none of which allocates:
-//   k_params : one CTA per unit: parameters (m_min, e, m) from two or more reductions over the
-//              unit's values, and its padded stream size written to out_off[u + 1];
+// Five launches on the caller's stream, none of which allocates:
+//   k_params_w / _b : parameters (m_min, e, m) of every unit and its padded stream size,
+//              written to out_off[u + 1]; a warp per unit of at most kSmall values, a CTA per
+//              larger unit;
 //   k_scan   : one CTA: in-place inclusive scan of the sizes into stream offsets;
-//   k_pack   : one CTA per unit, one thread per 32-bit output word: the codes overlapping the
-//              word are built and OR-ed together, so no two threads write the same word.
-// Arithmetic follows the host encoder operation by operation: |a| / m_min + 1 in two IEEE
-// round-to-nearest steps (__ddiv_rn, __dadd_rn), half-up rounding of the FP64 pattern to m
-// mantissa bits, FP32 / FP16 casts by the round-to-nearest-even conversions.
+//   k_pack_w / _b : the codes, 32 values at a time per warp: the 32 codes of a group fill
+//              exactly w 32-bit words, assembled in shared memory and stored whole (a warp per
+//              small unit, the warps of a CTA taking turns on a large one).
+// The results equal the host encoder's operation by operation: |a| / m_min + 1 in two IEEE
+// round-to-nearest steps, half-up rounding of the FP64 pattern to m mantissa bits, FP32 / FP16
+// casts by the round-to-nearest-even conversions. GB300's FP64 pipe is narrow, so the AFL
+// codes take the quotient from a per-unit reciprocal and fall back to the IEEE division only
+// where that approximation could round differently (see afl_rounded).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "hlr_internal.h"
@@ -23,8 +28,10 @@ namespace hlr {
 namespace {
 
 constexpr int kEncThreads = 256;
+constexpr int kEncWarps = kEncThreads / 32;
 
 __device__ __forceinline__ uint64_t d2u(double x) { return static_cast<uint64_t>(__double_as_longlong(x)); }
+__device__ __forceinline__ double u2d(uint64_t b) { return __longlong_as_double(static_cast<long long>(b)); }
 
 // ceil(-log2 u) clamped to [0, 52] (u > 0 finite): u = f 2^E, f in [1/2, 1) gives 1 - E; for
 // a normal u with biased exponent b, E = b - 1022
@@ -34,9 +41,8 @@ __device__ __forceinline__ int mbits_of(double u) {
   const int m = 1023 - b;
   return m < 0 ? 0 : m > 52 ? 52 : m;
 }
-// FP64 pattern of v rounded half up to m mantissa bits (a carry runs into the exponent)
-__device__ __forceinline__ uint64_t round_bits(double v, int m) {
-  uint64_t b = d2u(v);
+// FP64 pattern b rounded half up to m mantissa bits (a carry runs into the exponent)
+__device__ __forceinline__ uint64_t round_pattern(uint64_t b, int m) {
   if (m < 52) {
     b += uint64_t(1) << (51 - m);
     b &= ~((uint64_t(1) << (52 - m)) - 1);
@@ -58,210 +64,326 @@ __device__ __forceinline__ uint32_t bfl_bits(double x, int mp) {
 // MP: IEEE width (16, 32, 64) of the cheapest format with unit roundoff <= u (Table 1)
 __device__ __forceinline__ int mp_bits(double u) { return u >= 0x1p-11 ? 16 : u >= 0x1p-24 ? 32 : 64; }
 
-// block-wide reductions (kEncThreads threads)
-__device__ double block_min(double v, double *sh) {
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = sh[0];
-  for (int k = 1; k < kEncThreads / 32; ++k) v = fmin(v, sh[k]);
-  return v;
+// v = RN(RN(av / m_min) + 1), exactly as the host computes it (av = |a| > 0 finite).
+__device__ __forceinline__ double afl_v_exact(double av, double m_min) {
+  return __dadd_rn(__ddiv_rn(av, m_min), 1.0);
 }
-__device__ long long block_max(long long v, long long *sh) {
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = sh[0];
-  for (int k = 1; k < kEncThreads / 32; ++k) v = max(v, sh[k]);
-  return v;
+// The pattern of v rounded half up to m bits, from the reciprocal r = RN(1 / m_min). The
+// quotient q0 = RN(av r) is within 3 ulps of RN(av / m_min) (r and the product each add at most
+// half an ulp of relative error), so RN(q0 + 1) is within 4 ulps of v (ulp(v) >= ulp(q)) and
+// its pattern within 8 units of v's (16 across a binade edge). The half-up rounding to m bits
+// only changes where the low 52 - m bits cross 2^(51 - m); when q0 + 1 lands farther than 32
+// units from that point (and m <= 46, so the low bits have room), both round alike. Elsewhere
+// the exact division decides: for m = 20 that is about one value in 2^26.
+__device__ __forceinline__ uint64_t afl_rounded(double av, double m_min, double r, int m) {
+  // (r must be a normal number for the error bound; a quotient that overflows goes the exact way)
+  const uint32_t re = uint32_t(d2u(r) >> 52) & 0x7ffu;
+  if (m <= 46 && re != 0 && re != 0x7ffu) {
+    const uint64_t b = d2u(__dadd_rn(__dmul_rn(av, r), 1.0));
+    const uint64_t low = b & ((uint64_t(1) << (52 - m)) - 1);
+    const uint64_t half = uint64_t(1) << (51 - m);
+    const uint64_t dist = low > half ? low - half : half - low;
+    if (dist > 32 && ((b >> 52) & 0x7ff) != 0x7ff) return round_pattern(b, m);
+  }
+  return round_pattern(d2u(afl_v_exact(av, m_min)), m);
 }
-__device__ int block_or(int v, int *sh) {
-  v = __reduce_or_sync(0xffffffffu, unsigned(v));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) sh[w] = v;
-  __syncthreads();
-  v = 0;
-  for (int k = 0; k < kEncThreads / 32; ++k) v |= sh[k];
+
+// Reductions over a group of NT threads that handles one unit: a warp (NT = 32: shuffles only)
+// or the whole CTA (NT = kEncThreads: shuffles, then one slot per warp in shared memory). Every
+// thread of the group gets the result.
+struct RedShared {
+  unsigned long long a[kEncWarps], b[kEncWarps];
+  int i[kEncWarps];
+};
+template <int NT>
+__device__ __forceinline__ int grp_rank() {
+  return NT == 32 ? int(threadIdx.x & 31) : int(threadIdx.x);
+}
+// (min of a, max of b) over the group
+template <int NT>
+__device__ void grp_minmax(unsigned long long &a, unsigned long long &b, RedShared *sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a = min(a, (unsigned long long)__shfl_xor_sync(0xffffffffu, a, o));
+    b = max(b, (unsigned long long)__shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if constexpr (NT != 32) {
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      sh->a[threadIdx.x >> 5] = a;
+      sh->b[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    a = sh->a[0];
+    b = sh->b[0];
+    for (int k = 1; k < NT / 32; ++k) {
+      a = min(a, sh->a[k]);
+      b = max(b, sh->b[k]);
+    }
+    __syncthreads();
+  }
+}
+template <int NT>
+__device__ int grp_or(int v, RedShared *sh) {
+  v = int(__reduce_or_sync(0xffffffffu, unsigned(v)));
+  if constexpr (NT != 32) {
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh->i[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = 0;
+    for (int k = 0; k < NT / 32; ++k) v |= sh->i[k];
+    __syncthreads();
+  }
   return v;
 }
 
 __device__ __forceinline__ int bit_length(unsigned long long x) { return x ? 64 - __clzll(x) : 0; }
 
-// largest exponent field of the AFL codes of a unit at m mantissa bits
-__device__ long long afl_fmax(const double *a, int64_t n, double m_min, int m, long long *sh) {
-  long long f = 0;
-  for (int64_t j = threadIdx.x; j < n; j += kEncThreads) {
-    const double v = __dadd_rn(__ddiv_rn(fabs(a[j]), m_min), 1.0);
-    f = max(f, (long long)(round_bits(v, m) >> 52) - 1023);
-  }
-  return block_max(f, sh);
-}
+// Units of at most kSmall values are handled by one warp each, larger ones by a whole CTA; both
+// kernels see every unit and take exactly the units of their class.
+constexpr int64_t kSmall = 2048;
+__device__ __forceinline__ bool small_unit(const int64_t *off, int64_t u) { return off[u + 1] - off[u] <= kSmall; }
 
-__global__ void __launch_bounds__(kEncThreads) k_params(int fmt, int64_t nunits, int64_t total,
-                                                         const int64_t *__restrict__ off,
-                                                         const double *__restrict__ a, const double *__restrict__ uprec,
-                                                         double *m_min_out, int32_t *e_out, int32_t *m_out,
-                                                         int64_t *out_off) {
-  __shared__ double shd[kEncThreads / 32];
-  __shared__ long long shl[kEncThreads / 32];
-  __shared__ int shi[kEncThreads / 32];
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int64_t j0 = off[u], n = off[u + 1] - j0;
-    const double *x = a + j0;
-    const double uu = uprec[u];
-    // a unit whose precision is not positive and finite, or whose offsets decrease or leave
-    // [0, total], is rejected (and its values are not read)
-    bool bad = !(uu > 0.0) || !(uu <= 1.7976931348623157e308) || n < 0 || j0 < 0 || off[u + 1] > total;
-    double m_min = 1.0;
-    int e = 0, m = 0, w = 1;
-    if (!bad && (fmt == HLR_FMT_AFL_APLR || fmt == HLR_FMT_AFLP)) {
-      m = mbits_of(uu);
-      double mn = __longlong_as_double(0x7ff0000000000000ll);  // +inf
-      int nf = 0;
-      for (int64_t j = threadIdx.x; j < n; j += kEncThreads) {
-        const double v = x[j];
-        const double av = fabs(v);
-        if (!(av <= 1.7976931348623157e308)) nf = 1;
-        if (av != 0.0) mn = fmin(mn, av);
-      }
-      bad = block_or(nf, shi) != 0;
-      mn = block_min(mn, shd);
-      if (!bad) {
-        if (!(mn <= 1.7976931348623157e308)) {  // all zero: e = 0 (AFLP still aligns 1 + m)
-          m_min = 0.0;
-          e = 0;
-          while (fmt == HLR_FMT_AFLP && (1 + m) % 8 != 0 && m < 52) ++m;
-        } else {
-          m_min = mn;
-          for (;; ++m) {
-            e = bit_length((unsigned long long)afl_fmax(x, n, mn, m, shl));
-            if (fmt == HLR_FMT_AFL_APLR || (1 + e + m) % 8 == 0 || m == 52) break;
-          }
-        }
-        w = 1 + e + m;
-      }
-    } else if (!bad) {
-      int over = 0;
-      if (fmt == HLR_FMT_BFL) {
-        const int mb = mbits_of(uu);
-        m = mb <= 7 ? 7 : mb <= 15 ? 15 : 23;
-        e = 8;
-        for (int64_t j = threadIdx.x; j < n; j += kEncThreads) {
-          const double v = x[j];
-          if (!(fabs(v) <= 1.7976931348623157e308) || ((bfl_bits(v, m) >> 23) & 0xffu) == 0xffu) over = 1;
-        }
-      } else if (fmt == HLR_FMT_DFL) {
-        const int mb = mbits_of(uu);
-        m = 4;
-        while (m < mb) m += 8;
-        e = 11;
-        for (int64_t j = threadIdx.x; j < n; j += kEncThreads)
-          if (((round_bits(x[j], m) >> 52) & 0x7ff) == 0x7ff) over = 1;  // also NaN / Inf input
-      } else {  // HLR_FMT_MP
-        const int bits = mp_bits(uu);
-        e = bits == 16 ? 5 : bits == 32 ? 8 : 11;
-        m = bits == 16 ? 10 : bits == 32 ? 23 : 52;
-        for (int64_t j = threadIdx.x; j < n; j += kEncThreads) {
-          const double v = x[j];
-          if (!(fabs(v) <= 1.7976931348623157e308)) over = 1;
-          if (bits == 32 && (f32_bits_rn(v) & 0x7f800000u) == 0x7f800000u) over = 1;
-          if (bits == 16 && (f16_bits_rn(v) & 0x7c00u) == 0x7c00u) over = 1;
+// parameters and padded stream size of unit u, computed by a group of NT threads
+template <int NT>
+__device__ void unit_params_dev(int fmt, int64_t u, int64_t total, const int64_t *__restrict__ off,
+                                const double *__restrict__ a, const double *__restrict__ uprec, double *m_min_out,
+                                int32_t *e_out, int32_t *m_out, int64_t *out_off, RedShared *sh) {
+  const int64_t j0 = off[u], n = off[u + 1] - j0;
+  const double uu = uprec[u];
+  // a unit whose precision is not positive and finite, or whose offsets decrease or leave
+  // [0, total], is rejected (and its values are not read)
+  bool bad = !(uu > 0.0) || !(uu <= 1.7976931348623157e308) || n < 0 || j0 < 0 || off[u + 1] > total;
+  const double *x = a + (bad ? 0 : j0);
+  double m_min = 1.0;
+  int e = 0, m = 0, w = 1;
+  if (!bad && (fmt == HLR_FMT_AFL_APLR || fmt == HLR_FMT_AFLP)) {
+    // Every rounding step of a code is monotone in |a|, so the largest exponent field is the
+    // field of the largest magnitude: one pass finds the smallest nonzero and the largest
+    // magnitude (non-negative doubles order like their bit patterns), one division per unit
+    // gives the field.
+    m = mbits_of(uu);
+    unsigned long long mn = ~0ull, mx = 0;
+    int nf = 0;
+    for (int64_t j = grp_rank<NT>(); j < n; j += NT) {
+      const unsigned long long b = d2u(x[j]) & 0x7fffffffffffffffull;
+      if (b >= 0x7ff0000000000000ull) nf = 1;
+      if (b != 0) mn = min(mn, b);
+      mx = max(mx, b);
+    }
+    bad = grp_or<NT>(nf, sh) != 0;
+    grp_minmax<NT>(mn, mx, sh);
+    if (!bad) {
+      if (mx == 0) {  // all zero: e = 0 (AFLP still aligns 1 + m)
+        m_min = 0.0;
+        e = 0;
+        while (fmt == HLR_FMT_AFLP && (1 + m) % 8 != 0 && m < 52) ++m;
+      } else {
+        m_min = u2d(mn);
+        const uint64_t vb = d2u(afl_v_exact(u2d(mx), m_min));
+        for (;; ++m) {
+          e = bit_length((unsigned long long)((round_pattern(vb, m) >> 52) - 1023));
+          if (fmt == HLR_FMT_AFL_APLR || (1 + e + m) % 8 == 0 || m == 52) break;
         }
       }
-      bad = block_or(over, shi) != 0;
       w = 1 + e + m;
     }
-    if (threadIdx.x == 0) {
-      m_min_out[u] = bad ? 0.0 : m_min;
-      e_out[u] = bad ? -1 : e;
-      m_out[u] = bad ? 0 : m;
-      out_off[u + 1] = bad ? 0 : int64_t(((uint64_t(n) * uint64_t(w) + 7) / 8 + 15) & ~uint64_t(15));
+  } else if (!bad) {
+    int over = 0;
+    if (fmt == HLR_FMT_BFL) {
+      const int mb = mbits_of(uu);
+      m = mb <= 7 ? 7 : mb <= 15 ? 15 : 23;
+      e = 8;
+      for (int64_t j = grp_rank<NT>(); j < n; j += NT) {
+        const double v = x[j];
+        if (!(fabs(v) <= 1.7976931348623157e308) || ((bfl_bits(v, m) >> 23) & 0xffu) == 0xffu) over = 1;
+      }
+    } else if (fmt == HLR_FMT_DFL) {
+      const int mb = mbits_of(uu);
+      m = 4;
+      while (m < mb) m += 8;
+      e = 11;
+      for (int64_t j = grp_rank<NT>(); j < n; j += NT)
+        if (((round_pattern(d2u(x[j]), m) >> 52) & 0x7ff) == 0x7ff) over = 1;  // also NaN / Inf input
+    } else {  // HLR_FMT_MP
+      const int bits = mp_bits(uu);
+      e = bits == 16 ? 5 : bits == 32 ? 8 : 11;
+      m = bits == 16 ? 10 : bits == 32 ? 23 : 52;
+      for (int64_t j = grp_rank<NT>(); j < n; j += NT) {
+        const double v = x[j];
+        if (!(fabs(v) <= 1.7976931348623157e308)) over = 1;
+        if (bits == 32 && (f32_bits_rn(v) & 0x7f800000u) == 0x7f800000u) over = 1;
+        if (bits == 16 && (f16_bits_rn(v) & 0x7c00u) == 0x7c00u) over = 1;
+      }
     }
+    bad = grp_or<NT>(over, sh) != 0;
+    w = 1 + e + m;
+  }
+  if (grp_rank<NT>() == 0) {
+    m_min_out[u] = bad ? 0.0 : m_min;
+    e_out[u] = bad ? -1 : e;
+    m_out[u] = bad ? 0 : m;
+    out_off[u + 1] = bad ? 0 : int64_t(((uint64_t(n) * uint64_t(w) + 7) / 8 + 15) & ~uint64_t(15));
+  }
+}
+
+// small units: one warp each
+__global__ void __launch_bounds__(kEncThreads) k_params_w(int fmt, int64_t nunits, int64_t total,
+                                                           const int64_t *__restrict__ off, const double *__restrict__ a,
+                                                           const double *__restrict__ uprec, double *m_min_out,
+                                                           int32_t *e_out, int32_t *m_out, int64_t *out_off) {
+  const int64_t nwarps = int64_t(gridDim.x) * kEncWarps;
+  for (int64_t u = int64_t(blockIdx.x) * kEncWarps + (threadIdx.x >> 5); u < nunits; u += nwarps)
+    if (small_unit(off, u)) unit_params_dev<32>(fmt, u, total, off, a, uprec, m_min_out, e_out, m_out, out_off, nullptr);
+}
+// large units: one CTA each
+__global__ void __launch_bounds__(kEncThreads) k_params_b(int fmt, int64_t nunits, int64_t total,
+                                                           const int64_t *__restrict__ off, const double *__restrict__ a,
+                                                           const double *__restrict__ uprec, double *m_min_out,
+                                                           int32_t *e_out, int32_t *m_out, int64_t *out_off) {
+  __shared__ RedShared sh;
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    if (small_unit(off, u)) continue;
+    unit_params_dev<kEncThreads>(fmt, u, total, off, a, uprec, m_min_out, e_out, m_out, out_off, &sh);
+  }
+}
+
+// in-place inclusive scan of out_off[1..nunits] into stream offsets (out_off[0] = 0), by one
+// CTA of kScanThreads threads walking tiles of kScanThreads * 4 entries: coalesced loads, a
+// scan of the tile in shared memory, the running total carried from tile to tile
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan(int64_t nunits, int64_t *out_off) {
+  __shared__ int64_t wsum[kScanThreads / 32];
+  __shared__ int64_t carry;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (t == 0) {
+    carry = 0;
+    out_off[0] = 0;
+  }
+  __syncthreads();
+  for (int64_t base = 1; base <= nunits; base += int64_t(kScanThreads) * 4) {
+    // thread t owns entries base + 4t .. base + 4t + 3
+    int64_t v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + 4 * int64_t(t) + k;
+      v[k] = i <= nunits ? out_off[i] : 0;
+      s += v[k];
+    }
+    // inclusive scan of the threads' sums: within the warp, then over the warps
+    int64_t x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int64_t w = lane < kScanThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      if (lane < kScanThreads / 32) wsum[lane] = w;
+    }
+    __syncthreads();
+    int64_t run = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;  // exclusive prefix of thread t
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t i = base + 4 * int64_t(t) + k;
+      run += v[k];
+      if (i <= nunits) out_off[i] = run;
+    }
+    __syncthreads();
+    if (t == kScanThreads - 1) carry = run;
     __syncthreads();
   }
 }
 
-// in-place inclusive scan of out_off[1..nunits] (one CTA of kEncThreads threads; out_off[0] = 0)
-__global__ void __launch_bounds__(kEncThreads) k_scan(int64_t nunits, int64_t *out_off) {
-  __shared__ int64_t part[kEncThreads];
-  const int64_t per = (nunits + kEncThreads - 1) / kEncThreads;
-  const int64_t b = 1 + int64_t(threadIdx.x) * per, e = min(nunits + 1, b + per);
-  int64_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += out_off[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t run = 0;
-    for (int k = 0; k < kEncThreads; ++k) {
-      const int64_t t = part[k];
-      part[k] = run;
-      run += t;
-    }
-    out_off[0] = 0;
-  }
-  __syncthreads();
-  int64_t run = part[threadIdx.x];
-  for (int64_t i = b; i < e; ++i) {
-    run += out_off[i];
-    out_off[i] = run;
-  }
-}
-
-// code of value x of a unit (w = 1 + e + m bits, low bits of the result)
-__device__ __forceinline__ uint64_t code_of(int fmt, double x, double m_min, int e, int m) {
+// code of value x of a unit (w = 1 + e + m bits, low bits of the result); r = RN(1 / m_min)
+__device__ __forceinline__ uint64_t code_of(int fmt, double x, double m_min, double r, int e, int m) {
   if (fmt == HLR_FMT_AFL_APLR || fmt == HLR_FMT_AFLP) {
-    if (m_min == 0.0) return 0;
-    const double v = __dadd_rn(__ddiv_rn(fabs(x), m_min), 1.0);
-    const uint64_t b = round_bits(v, m);
+    const double av = fabs(x);
+    if (m_min == 0.0 || av == 0.0) return 0;  // v = 1: field 0, mantissa 0, no sign
+    const uint64_t b = afl_rounded(av, m_min, r, m);
     const uint64_t field = (b >> 52) - 1023;
     const uint64_t mant = (b & ((uint64_t(1) << 52) - 1)) >> (52 - m);
     const uint64_t sign = x < 0.0 ? 1 : 0;
     return (sign << (e + m)) | (field << m) | mant;
   }
   if (fmt == HLR_FMT_BFL) return uint64_t(bfl_bits(x, m) >> (23 - m));
-  if (fmt == HLR_FMT_DFL) return round_bits(x, m) >> (52 - m);
+  if (fmt == HLR_FMT_DFL) return round_pattern(d2u(x), m) >> (52 - m);
   // HLR_FMT_MP
   if (e == 5) return f16_bits_rn(x);
   if (e == 8) return f32_bits_rn(x);
   return d2u(x);
 }
 
-__global__ void __launch_bounds__(kEncThreads) k_pack(int fmt, int64_t nunits, const int64_t *__restrict__ off,
-                                                       const double *__restrict__ a, const double *__restrict__ m_min_in,
-                                                       const int32_t *__restrict__ e_in, const int32_t *__restrict__ m_in,
-                                                       const int64_t *__restrict__ out_off, uint8_t *out, uint64_t cap) {
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int e = e_in[u];
-    if (e < 0) continue;
-    const int m = m_in[u], w = 1 + e + m;
-    const double m_min = m_min_in[u];
-    const int64_t j0 = off[u], n = off[u + 1] - j0;
-    const uint64_t o0 = uint64_t(out_off[u]), o1 = uint64_t(out_off[u + 1]);
-    if (o1 > cap || o1 < o0) continue;  // unreachable when cap holds the bound the host checked
-    const double *x = a + j0;
-    uint32_t *dst = reinterpret_cast<uint32_t *>(out + o0);
-    const uint64_t nw = (o1 - o0) / 4;
-    const uint64_t nbits = uint64_t(n) * uint64_t(w);
-    for (uint64_t k = threadIdx.x; k < nw; k += kEncThreads) {
-      const uint64_t lo = 32 * k;
-      uint32_t word = 0;
-      if (lo < nbits) {
-        const uint64_t jb = lo / uint64_t(w);
-        const uint64_t je = min((lo + 31) / uint64_t(w), uint64_t(n) - 1);
-        for (uint64_t j = jb; j <= je; ++j) {
-          const uint64_t code = code_of(fmt, x[j], m_min, e, m);
-          const int64_t sh = int64_t(j * uint64_t(w)) - int64_t(lo);  // code bit 0 relative to the word
-          word |= sh >= 0 ? uint32_t(code << sh) : uint32_t(code >> (-sh));
-        }
-      }
-      dst[k] = word;
+// Groups g0, g0 + gs, ... of 32 values of unit u, one warp: lane l builds the code of value
+// 32 g + l, ORs its (up to three) word parts into the warp's buffer of w words, and the warp
+// stores the w words (clipped to the unit's padded stream, whose tail words are zeroed).
+__device__ void pack_groups(int fmt, int64_t u, int64_t g0, int64_t gs, const int64_t *__restrict__ off,
+                            const double *__restrict__ a, const double *__restrict__ m_min_in,
+                            const int32_t *__restrict__ e_in, const int32_t *__restrict__ m_in,
+                            const int64_t *__restrict__ out_off, uint8_t *out, uint64_t cap, uint32_t *buf) {
+  const int lane = threadIdx.x & 31;
+  const int e = e_in[u];
+  if (e < 0) return;
+  const int m = m_in[u], w = 1 + e + m;
+  const double m_min = m_min_in[u];
+  const double r = m_min != 0.0 ? __drcp_rn(m_min) : 0.0;
+  const int64_t j0 = off[u], n = off[u + 1] - j0;
+  const uint64_t o0 = uint64_t(out_off[u]), o1 = uint64_t(out_off[u + 1]);
+  if (o1 > cap || o1 < o0) return;  // unreachable when cap holds the bound the host checked
+  const double *x = a + j0;
+  uint32_t *dst = reinterpret_cast<uint32_t *>(out + o0);
+  const int64_t nw = int64_t((o1 - o0) / 4);
+  const int64_t ngroups = (n + 31) / 32;
+  for (int64_t g = g0; g < ngroups; g += gs) {
+    for (int k = lane; k < w; k += 32) buf[k] = 0;
+    __syncwarp();
+    const int64_t j = 32 * g + lane;
+    if (j < n) {
+      const uint64_t code = code_of(fmt, x[j], m_min, r, e, m);
+      const int bit = lane * w;  // within the group's w words
+      const int q = bit >> 5, s = bit & 31;
+      const uint64_t lo = code << s;
+      const uint32_t p0 = uint32_t(lo), p1 = uint32_t(lo >> 32), p2 = s ? uint32_t(code >> (64 - s)) : 0u;
+      if (p0) atomicOr(&buf[q], p0);
+      if (p1) atomicOr(&buf[q + 1], p1);
+      if (p2) atomicOr(&buf[q + 2], p2);
     }
+    __syncwarp();
+    const int64_t wbase = g * w;
+    for (int k = lane; k < w; k += 32)
+      if (wbase + k < nw) dst[wbase + k] = buf[k];
+    __syncwarp();
   }
+  // words of the padded stream past the last group (written by the group-0 warp)
+  if (g0 == 0)
+    for (int64_t k = ngroups * w + lane; k < nw; k += 32) dst[k] = 0u;
+}
+
+__global__ void __launch_bounds__(kEncThreads) k_pack_w(int fmt, int64_t nunits, const int64_t *__restrict__ off,
+                                                         const double *__restrict__ a, const double *__restrict__ m_min_in,
+                                                         const int32_t *__restrict__ e_in, const int32_t *__restrict__ m_in,
+                                                         const int64_t *__restrict__ out_off, uint8_t *out, uint64_t cap) {
+  __shared__ uint32_t bufs[kEncWarps][68];
+  uint32_t *buf = bufs[threadIdx.x >> 5];
+  const int64_t nwarps = int64_t(gridDim.x) * kEncWarps;
+  for (int64_t u = int64_t(blockIdx.x) * kEncWarps + (threadIdx.x >> 5); u < nunits; u += nwarps)
+    if (small_unit(off, u)) pack_groups(fmt, u, 0, 1, off, a, m_min_in, e_in, m_in, out_off, out, cap, buf);
+}
+__global__ void __launch_bounds__(kEncThreads) k_pack_b(int fmt, int64_t nunits, const int64_t *__restrict__ off,
+                                                         const double *__restrict__ a, const double *__restrict__ m_min_in,
+                                                         const int32_t *__restrict__ e_in, const int32_t *__restrict__ m_in,
+                                                         const int64_t *__restrict__ out_off, uint8_t *out, uint64_t cap) {
+  __shared__ uint32_t bufs[kEncWarps][68];
+  uint32_t *buf = bufs[threadIdx.x >> 5];
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x)
+    if (!small_unit(off, u))
+      pack_groups(fmt, u, threadIdx.x >> 5, kEncWarps, off, a, m_min_in, e_in, m_in, out_off, out, cap, buf);
 }
 
 }  // namespace
@@ -286,10 +408,22 @@ extern "C" int hlr_encode_device(int32_t fmt, int64_t nunits, const int64_t *off
   if (double(cap) < need) return set_error(HLR_ERR_OOM, "hlr_encode_device: cap below 8 total_values + 16 nunits");
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   cudaGetLastError();
-  const unsigned grid = unsigned(nunits < (int64_t(1) << 30) ? nunits : (int64_t(1) << 30));
-  k_params<<<grid, kEncThreads, 0, st>>>(fmt, nunits, total_values, off_dev, a_dev, u_dev, m_min_dev, e_dev, m_dev, out_off_dev);
-  k_scan<<<1, kEncThreads, 0, st>>>(nunits, out_off_dev);
-  k_pack<<<grid, kEncThreads, 0, st>>>(fmt, nunits, off_dev, a_dev, m_min_dev, e_dev, m_dev, out_off_dev, out_dev,
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  // grid-stride launches: 8 CTAs per SM (a warp per small unit), 4 CTAs per SM (a CTA per
+  // large unit), capped by the units
+  const unsigned gw = unsigned(std::min<int64_t>((nunits + kEncWarps - 1) / kEncWarps, int64_t(sms) * 8));
+  const unsigned gb = unsigned(std::min<int64_t>(nunits, int64_t(sms) * 4));
+  k_params_w<<<gw, kEncThreads, 0, st>>>(fmt, nunits, total_values, off_dev, a_dev, u_dev, m_min_dev, e_dev, m_dev,
+                                         out_off_dev);
+  k_params_b<<<gb, kEncThreads, 0, st>>>(fmt, nunits, total_values, off_dev, a_dev, u_dev, m_min_dev, e_dev, m_dev,
+                                         out_off_dev);
+  k_scan<<<1, kScanThreads, 0, st>>>(nunits, out_off_dev);
+  k_pack_w<<<gw, kEncThreads, 0, st>>>(fmt, nunits, off_dev, a_dev, m_min_dev, e_dev, m_dev, out_off_dev, out_dev,
+                                       uint64_t(cap));
+  k_pack_b<<<gb, kEncThreads, 0, st>>>(fmt, nunits, off_dev, a_dev, m_min_dev, e_dev, m_dev, out_off_dev, out_dev,
                                        uint64_t(cap));
   const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string("hlr_encode_device: ") + cudaGetErrorString(err));

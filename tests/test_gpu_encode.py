@@ -92,3 +92,30 @@ def test_encode_device_graph_capture(exp2d_case):
     torch.cuda.synchronize()
     n = int(eager[3][-1])
     assert torch.equal(eager[4][:n], cap[4][:n]) and torch.equal(eager[3], cap[3])
+
+
+@pytest.mark.parametrize("fmt", ["afl", "aflp"])
+def test_encode_device_rounding_boundaries(fmt):
+    """Values whose scaled magnitude |a| / m_min + 1 lies at or within a few ulps of the half-way
+    point of the m-bit rounding (Section 3.2), for every m from 0 to 52, plus random values:
+    the GPU quotient must round exactly like the IEEE division of the host encoder."""
+    g = np.random.default_rng(41)
+    units, precs = [], []
+    for m in range(0, 53):
+        u = 2.0 ** -m
+        for m_min in (3.0, 0.7, 1.0 / 3.0, 5e-200, 7e150):
+            k = g.integers(0, 2 ** min(m, 40), 200).astype(np.float64)
+            v = (1.0 + (2.0 * k + 1.0) * 2.0 ** -(m + 1)) * 2.0 ** g.integers(1, 12, k.size)  # half-way at m bits
+            v = v * (1.0 + g.integers(-6, 7, k.size) * 2.0 ** -52)                      # and a few ulps off
+            t = v - 1.0
+            a = np.concatenate([[m_min], m_min * t, -m_min * t[::3]])
+            a = a[np.isfinite(a)]
+            units.append(a)
+            precs.append(u)
+        units.append(g.standard_normal(777) * np.exp(g.uniform(-8, 8, 777)))
+        precs.append(u)
+    vals = np.concatenate(units)
+    off = np.zeros(len(units) + 1, dtype=np.int64)
+    np.cumsum([x.size for x in units], out=off[1:])
+    ref = [afl.encode(x, p, fmt) for x, p in zip(units, precs)]
+    _check_units(vals, off, np.array(precs), fmt, ref)
