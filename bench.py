@@ -159,9 +159,11 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def recorded_traffic(kernel: str) -> dict | None:
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel source (matched by the source hash recorded beside it)."""
+def recorded_traffic(kernel: str, alg_bytes: float, eps: float) -> float | None:
+    """DRAM bytes per launch of `kernel` from the committed ncu capture: its traffic / algorithmic
+    ratio times this launch's algorithmic bytes (traffic grows with the units a launch processes),
+    if the capture was taken on the current kernel source (matched by the source hash recorded
+    beside it) and at the same eps (the code widths set the padding). None otherwise."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -171,9 +173,9 @@ def recorded_traffic(kernel: str) -> dict | None:
     src = os.path.join(ROOT, "paper_2308_10960_gb300", "csrc", "hlr_kernels.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     e = d.get(kernel)
-    if not e or e.get("source_sha256_16") != h:
+    if not e or e.get("source_sha256_16") != h or abs(e.get("captured_eps", -1.0) - eps) > 1e-12 * eps:
         return None
-    return e
+    return float(e["traffic_over_algorithmic"]) * alg_bytes
 
 
 def multi_rhs_bytes(info: dict, n: int, r: int) -> float:
@@ -345,9 +347,9 @@ def run_ours(args, world: int, rank: int, local: int):
     dom = int(np.argmax(kms))
     avg_ms = kms[dom] / max(calls, 1)
     achieved = k_bytes[dom] / (avg_ms / 1e3) / 1e9
-    tr = recorded_traffic(k_names[dom])
+    tr = recorded_traffic(k_names[dom], k_bytes[dom], args.eps)
     roofline = {"bound": "hbm", "kernel": k_names[dom], "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr["dram_bytes_per_launch"] if tr else None,
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
                 "peak_source": f"{peaks['source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_launch": k_bytes[dom],
                 "kernel_ms_avg": {k: m / max(calls, 1) for k, m in zip(k_names, kms)},
