@@ -162,14 +162,24 @@ __device__ void unit_params_dev(int fmt, int64_t u, int64_t total, const int64_t
     // magnitude (non-negative doubles order like their bit patterns), one division per unit
     // gives the field.
     m = mbits_of(uu);
-    unsigned long long mn = ~0ull, mx = 0;
+    // (per value in 32-bit halves: 64-bit integer operations would share GB300's narrow FP64
+    // pipe)
+    uint32_t mnh = 0xffffffffu, mnl = 0xffffffffu, mxh = 0, mxl = 0;
     int nf = 0;
     for (int64_t j = grp_rank<NT>(); j < n; j += NT) {
-      const unsigned long long b = d2u(x[j]) & 0x7fffffffffffffffull;
-      if (b >= 0x7ff0000000000000ull) nf = 1;
-      if (b != 0) mn = min(mn, b);
-      mx = max(mx, b);
+      const double v = x[j];
+      const uint32_t h = uint32_t(__double2hiint(v)) & 0x7fffffffu, l = uint32_t(__double2loint(v));
+      if (h >= 0x7ff00000u) nf = 1;
+      if (h > mxh || (h == mxh && l > mxl)) {
+        mxh = h;
+        mxl = l;
+      }
+      if ((h | l) != 0u && (h < mnh || (h == mnh && l < mnl))) {
+        mnh = h;
+        mnl = l;
+      }
     }
+    unsigned long long mn = (uint64_t(mnh) << 32) | mnl, mx = (uint64_t(mxh) << 32) | mxl;
     bad = grp_or<NT>(nf, sh) != 0;
     grp_minmax<NT>(mn, mx, sh);
     if (!bad) {
@@ -301,6 +311,51 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int64_t nunits, int64_t *
   }
 }
 
+// AFL code of x for a unit with w = 1 + e + m <= 32 in 32-bit integer operations (64-bit ones
+// would share GB300's narrow FP64 pipe with the two FP64 operations of the quotient), by the
+// reasoning of afl_rounded: the pattern b of RN(|x| r + 1) rounds like v unless (b + half + 32)
+// mod L <= 64 (L = 2^(52 - m), half = L / 2); then, and when the unit cannot take the fast path
+// (fast = false: m >= 46, r not normal), the IEEE division decides.
+__device__ __forceinline__ uint32_t afl_code32(double x, double m_min, double r, bool fast, int e, int m) {
+  const uint32_t xh = uint32_t(__double2hiint(x)), xl = uint32_t(__double2loint(x));
+  const uint32_t ah = xh & 0x7fffffffu;
+  if ((ah | xl) == 0u) return 0u;  // v = 1: field 0, mantissa 0, no sign
+  const double av = __hiloint2double(int(ah), int(xl));
+  uint32_t bh = 0, bl = 0;
+  bool near = !fast;
+  if (fast) {
+    const double v0 = __dadd_rn(__dmul_rn(av, r), 1.0);
+    bh = uint32_t(__double2hiint(v0));
+    bl = uint32_t(__double2loint(v0));
+    if ((bh >> 20) >= 0x7ffu) {
+      near = true;  // the approximate quotient overflowed
+    } else if (m < 20) {
+      // L > 2^32: the low bits are (bh mod 2^(20 - m), bl); half = 2^(19 - m) in the high word
+      const uint32_t cl = bl + 32u;
+      const uint32_t ch = (bh + (1u << (19 - m)) + (cl < 32u ? 1u : 0u)) & ((1u << (20 - m)) - 1u);
+      near = ch == 0u && cl <= 64u;
+      bh = (bh + (1u << (19 - m))) & ~((1u << (20 - m)) - 1u);
+      bl = 0u;
+    } else {
+      const int sh = 52 - m;  // 21 .. 32 (m <= 31 here)
+      const uint32_t lmask = sh >= 32 ? 0xffffffffu : (1u << sh) - 1u;
+      const uint32_t half = 1u << (sh - 1);
+      near = ((bl + half + 32u) & lmask) <= 64u;
+      const uint32_t t = bl + half;
+      bh += t < bl ? 1u : 0u;
+      bl = t & ~lmask;
+    }
+  }
+  if (near) {
+    const uint64_t b = round_pattern(d2u(afl_v_exact(av, m_min)), m);
+    bh = uint32_t(b >> 32);
+    bl = uint32_t(b);
+  }
+  const uint32_t field = (bh >> 20) - 1023u;
+  const uint32_t mant = m <= 20 ? (bh & 0xfffffu) >> (20 - m) : ((bh & 0xfffffu) << (m - 20)) | (bl >> (52 - m));
+  return ((xh >> 31) << (e + m)) | (field << m) | mant;
+}
+
 // code of value x of a unit (w = 1 + e + m bits, low bits of the result); r = RN(1 / m_min)
 __device__ __forceinline__ uint64_t code_of(int fmt, double x, double m_min, double r, int e, int m) {
   if (fmt == HLR_FMT_AFL_APLR || fmt == HLR_FMT_AFLP) {
@@ -333,6 +388,10 @@ __device__ void pack_groups(int fmt, int64_t u, int64_t g0, int64_t gs, const in
   const int m = m_in[u], w = 1 + e + m;
   const double m_min = m_min_in[u];
   const double r = m_min != 0.0 ? __drcp_rn(m_min) : 0.0;
+  const bool afl = fmt == HLR_FMT_AFL_APLR || fmt == HLR_FMT_AFLP;
+  const bool narrow = w <= 32 && fmt != HLR_FMT_DFL && !(afl && m_min == 0.0);
+  const uint32_t re = uint32_t(d2u(r) >> 52) & 0x7ffu;
+  const bool fast = m <= 45 && re != 0 && re != 0x7ffu;
   const int64_t j0 = off[u], n = off[u + 1] - j0;
   const uint64_t o0 = uint64_t(out_off[u]), o1 = uint64_t(out_off[u + 1]);
   if (o1 > cap || o1 < o0) return;  // unreachable when cap holds the bound the host checked
@@ -345,14 +404,21 @@ __device__ void pack_groups(int fmt, int64_t u, int64_t g0, int64_t gs, const in
     __syncwarp();
     const int64_t j = 32 * g + lane;
     if (j < n) {
-      const uint64_t code = code_of(fmt, x[j], m_min, r, e, m);
       const int bit = lane * w;  // within the group's w words
       const int q = bit >> 5, s = bit & 31;
-      const uint64_t lo = code << s;
-      const uint32_t p0 = uint32_t(lo), p1 = uint32_t(lo >> 32), p2 = s ? uint32_t(code >> (64 - s)) : 0u;
-      if (p0) atomicOr(&buf[q], p0);
-      if (p1) atomicOr(&buf[q + 1], p1);
-      if (p2) atomicOr(&buf[q + 2], p2);
+      if (narrow) {  // a 32-bit code: at most two words
+        const uint32_t code = afl ? afl_code32(x[j], m_min, r, fast, e, m) : uint32_t(code_of(fmt, x[j], m_min, r, e, m));
+        const uint32_t p0 = code << s, p1 = s ? code >> (32 - s) : 0u;
+        if (p0) atomicOr(&buf[q], p0);
+        if (p1) atomicOr(&buf[q + 1], p1);
+      } else {
+        const uint64_t code = code_of(fmt, x[j], m_min, r, e, m);
+        const uint64_t lo = code << s;
+        const uint32_t p0 = uint32_t(lo), p1 = uint32_t(lo >> 32), p2 = s ? uint32_t(code >> (64 - s)) : 0u;
+        if (p0) atomicOr(&buf[q], p0);
+        if (p1) atomicOr(&buf[q + 1], p1);
+        if (p2) atomicOr(&buf[q + 2], p2);
+      }
     }
     __syncwarp();
     const int64_t wbase = g * w;
