@@ -173,6 +173,7 @@ struct ColDec {
   uint32_t e, m, w;
   bool fast32;       // w <= 32, m <= 23, e <= 7: FP32 bit pattern built with integer ops
   bool narrow;       // w <= 32: a code fits a two-word window
+  bool mid32;        // w <= 32 and (fast32 or e <= 4): dec_mid32 gives the FP64 route's value
 };
 
 __device__ __forceinline__ ColDec col_dec(uint32_t e, uint32_t m) {
@@ -186,7 +187,24 @@ __device__ __forceinline__ ColDec col_dec(uint32_t e, uint32_t m) {
   c.sshift = em <= 31 ? 31 - em : 0;
   c.fast32 = (c.w <= 32) && (m <= 23) && (e <= 7);
   c.narrow = c.w <= 32;
+  c.mid32 = c.fast32 || (c.narrow && e <= 4);
   return c;
+}
+
+// +-(v - 1) rounded once to FP32 (the value the FP64 route float(dec_f64(code)) gives) for a
+// code of w <= 32 bits whose mantissa may be wider than FP32's (m up to 31): v's top 23
+// mantissa bits form an FP32 v_hi, v_hi - 1 is exact while the field is below 2^4 (e <= 4; for
+// m <= 23, v_hi = v and any e of fast32 works), and the remaining m - 23 bits, an exact FP32
+// lo * 2^(field - m), are added with the one rounding.
+__device__ __forceinline__ float dec_mid32(uint32_t code, const ColDec &c) {
+  const uint32_t m = c.m;
+  const uint32_t mant = code & (m ? 0xffffffffu >> (32 - m) : 0u);
+  const uint32_t field = (code >> m) & ((1u << c.e) - 1u);
+  const uint32_t k = m > 23 ? m - 23 : 0u;
+  const uint32_t hi = m > 23 ? mant >> k : mant << (23 - m);
+  const float lo = __uint2float_rn(mant & ((1u << k) - 1u)) * __uint_as_float((field + 127u - m) << 23);
+  const float r = (__uint_as_float(((field + 127u) << 23) | hi) - 1.0f) + lo;
+  return ((code >> (c.e + m)) & 1u) ? -r : r;
 }
 
 // +-(v - 1) as FP32 (fast path: integer ops build the FP32 pattern of v)
@@ -554,6 +572,14 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
 #pragma unroll 8
                 for (int r = 0; r < rc; ++r, bit += c.w, xa += xstep)
                   dot = fmaf(val32<FMT>(bc_code32_s(col_s, bit), c), ld_shared_f32(xa), dot);
+              } else if (FMT == FMT_AFL32 && c.mid32) {
+                // mantissas wider than FP32's: the FP64 route's values from FP32 operations
+                const uint32_t col_s = smem_u32(col);
+                const uint32_t xstep = uint32_t(xs) * 4u;
+                uint32_t xa = smem_u32(xr);
+#pragma unroll 4
+                for (int r = 0; r < rc; ++r, bit += c.w, xa += xstep)
+                  dot = fmaf(dec_mid32(bc_code32_s(col_s, bit), c), ld_shared_f32(xa), dot);
               } else {
                 for (int r = 0; r < rc; ++r, bit += c.w)
                   dot = fmaf(float(dec_any64(bc_code32(col, bit), c, kVF<FMT>)), xr[r * xs], dot);
@@ -647,9 +673,12 @@ __device__ __forceinline__ void slice_setup(const Seg &sg, int j, int nr, const 
 // added in FP64, in fixed order, into y.
 // ---------------------------------------------------------------------------------------------
 // rows [0, nr) of the lane's slice into acc[r]; rows past the leaf decode the slice's first value
-// (in bounds) and are dropped. GEN: the generic FP64 decode (wide codes, large e or m).
-template <bool GEN, int FMT>
+// (in bounds) and are dropped. MODE 0: the FP32 bit-pattern decode; 1: dec_mid32 (the FP64
+// route's values, for warps with mantissas wider than FP32's); 2 (GEN): the generic FP64 decode
+// (codes wider than 32 bits, large e).
+template <int MODE, int FMT>
 __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t *col, const ColDec &c, float mult) {
+  constexpr bool GEN = MODE == 2;
   const uint32_t col_s = smem_u32(col);  // 32-bit shared-memory address of the lane column
   // chunks of 8 rows: leaves of the cluster tree hold 32..64 rows, so a row count that is not a
   // multiple of the chunk costs at most 7 predicated decodes
@@ -659,15 +688,19 @@ __device__ __forceinline__ void p2_rows(float (&acc)[64], int nr, const uint32_t
     if (!GEN && 8 * k + 8 <= nr) {  // a whole chunk of the leaf: no row checks
       uint32_t bit = uint32_t(8 * k) * c.w;
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr, bit += c.w) acc[8 * k + rr] += valmul32<FMT>(bc_code32_s(col_s, bit), c, mult);
+      for (int rr = 0; rr < 8; ++rr, bit += c.w) {
+        const uint32_t code = bc_code32_s(col_s, bit);
+        acc[8 * k + rr] += MODE == 1 ? dec_mid32(code, c) * mult : valmul32<FMT>(code, c, mult);
+      }
     } else {
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const int r = 8 * k + rr;
         const bool ok = r < nr;
         const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
-        const float p = GEN ? float(dec_any64(bc_code64(col, bit), c, kVF<FMT>)) * mult
-                            : valmul32<FMT>(bc_code32_s(col_s, bit), c, mult);
+        const float p = GEN         ? float(dec_any64(bc_code64(col, bit), c, kVF<FMT>)) * mult
+                        : MODE == 1 ? dec_mid32(bc_code32_s(col_s, bit), c) * mult
+                                    : valmul32<FMT>(bc_code32_s(col_s, bit), c, mult);
         if (ok) acc[r] += p;
       }
     }
@@ -722,11 +755,15 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
     }
     const ColDec c = lane_dec(hd);
     const bool fast = __all_sync(kFull, !active || fast_dec<FMT>(c));  // FP32 bit-pattern decode
+    // AFL codes with mantissas wider than FP32's: the FP64 route's values from FP32 operations
+    const bool mid = FMT == FMT_AFL32 && !fast && __all_sync(kFull, !active || c.mid32);
     if (active) {
       if (fast)
-        p2_rows<false, FMT>(acc, nr, col, c, mult);
+        p2_rows<0, FMT>(acc, nr, col, c, mult);
+      else if (mid)
+        p2_rows<1, FMT>(acc, nr, col, c, mult);
       else
-        p2_rows<true, FMT>(acc, nr, col, c, mult);
+        p2_rows<2, FMT>(acc, nr, col, c, mult);
     }
     if (flags & PF_END_LEAF) {
       // reduce-scatter over the warp: 5 halving stages (stage s keeps the upper half of the
