@@ -162,24 +162,14 @@ __device__ void unit_params_dev(int fmt, int64_t u, int64_t total, const int64_t
     // magnitude (non-negative doubles order like their bit patterns), one division per unit
     // gives the field.
     m = mbits_of(uu);
-    // (per value in 32-bit halves: 64-bit integer operations would share GB300's narrow FP64
-    // pipe)
-    uint32_t mnh = 0xffffffffu, mnl = 0xffffffffu, mxh = 0, mxl = 0;
+    unsigned long long mn = ~0ull, mx = 0;
     int nf = 0;
     for (int64_t j = grp_rank<NT>(); j < n; j += NT) {
-      const double v = x[j];
-      const uint32_t h = uint32_t(__double2hiint(v)) & 0x7fffffffu, l = uint32_t(__double2loint(v));
-      if (h >= 0x7ff00000u) nf = 1;
-      if (h > mxh || (h == mxh && l > mxl)) {
-        mxh = h;
-        mxl = l;
-      }
-      if ((h | l) != 0u && (h < mnh || (h == mnh && l < mnl))) {
-        mnh = h;
-        mnl = l;
-      }
+      const unsigned long long b = d2u(x[j]) & 0x7fffffffffffffffull;
+      if (b >= 0x7ff0000000000000ull) nf = 1;
+      if (b != 0) mn = min(mn, b);
+      mx = max(mx, b);
     }
-    unsigned long long mn = (uint64_t(mnh) << 32) | mnl, mx = (uint64_t(mxh) << 32) | mxl;
     bad = grp_or<NT>(nf, sh) != 0;
     grp_minmax<NT>(mn, mx, sh);
     if (!bad) {
