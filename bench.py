@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
     ap.add_argument("--serve-rates", default="20,100,500", help="arrival rates (requests/s) to sweep")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-solve-frac", type=float, default=0.3, help="share of CG solves among the requests")
     return ap.parse_args()
 
 
@@ -557,9 +558,10 @@ def run_batch(args, world: int, rank: int, local: int):
 def run_serve(args, world: int, rank: int, local: int):
     """Serving: --serve-mats Matern matrices (n log-spaced in [--serve-min-n, --serve-max-n],
     points seed 200 + i) resident under an HBM budget; for every arrival rate a Poisson stream
-    (seed 5) of --serve-requests requests, 70 % products and 30 % CG solves to 1e-8, over the
-    matrices uniformly (seed 6). value = products' and solves' algorithmic bytes / makespan at the
-    highest rate; p50/p99 latency per rate and kind."""
+    (seed 5) of --serve-requests requests, CG solves to 1e-8 with probability --serve-solve-frac
+    (default 0.3) and products otherwise, over the matrices uniformly (seed 6). value = products'
+    and solves' algorithmic bytes / makespan at the highest rate; p50/p99 latency per rate and
+    kind."""
     import torch
     import synth
     import paper_2308_10960_gb300 as hg
@@ -591,12 +593,22 @@ def run_serve(args, world: int, rank: int, local: int):
         reqs = []
         for i in range(args.serve_requests):
             m = names[int(g.integers(len(names)))]
-            kind = "solve" if g.random() < 0.3 else "matvec"
+            kind = "solve" if g.random() < args.serve_solve_frac else "matvec"
             x = torch.from_numpy(synth.rhs(host[m].n, 7000 + 100 * ri + i)).to(dev)
             reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000))
         torch.cuda.synchronize()
         srv = serve.Server(be, budget_bytes=budget, cg_workers=4, max_rhs=32)
         srv.preload(names)           # the matrices are resident before the requests arrive
+        if ri == 0:
+            # warm-up, untimed: every matrix takes one product and a few CG iterations, so that
+            # kernels are loaded and per-matrix scratch exists before the first timed request
+            warm = []
+            for i, m in enumerate(names):
+                xw = torch.from_numpy(synth.rhs(host[m].n, 9000 + i)).to(dev)
+                warm.append(serve.Request(-1 - 2 * i, "matvec", m, xw, arrival=0.0))
+                warm.append(serve.Request(-2 - 2 * i, "solve", m, xw, arrival=0.0, rtol=1e-8, maxit=3))
+            torch.cuda.synchronize()
+            srv.run(warm, realtime=False)
         torch.cuda.synchronize()
         st = srv.run(reqs)
         d = st.as_dict()
@@ -612,7 +624,8 @@ def run_serve(args, world: int, rank: int, local: int):
                "steps": args.serve_requests, "warmup": 0, "ms_per_step": last["makespan_s"] * 1e3 / args.serve_requests,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": f"serving {k} Matern nu=1.5 matrices n {sizes[0]}..{sizes[-1]}, eps={args.eps:g}, "
-                                      f"Poisson arrivals, 70% products / 30% CG to 1e-8, budget {args.serve_budget_gb:g} GB",
+                                      f"Poisson arrivals, {100 - 100 * args.serve_solve_frac:g}% products / "
+                                      f"{100 * args.serve_solve_frac:g}% CG to 1e-8, budget {args.serve_budget_gb:g} GB",
                           "sizes": sizes, "rates": rates, "requests_per_rate": args.serve_requests,
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "p99_solve_ms": solve_p99, "per_rate": per_rate, "pct_hbm_peak": last["GB/s"] / peaks["hbm_gbs"],
