@@ -300,6 +300,16 @@ int hlr_host_describe(const hlr_host_hmatrix *hm, hlr_hmatrix_desc *d);
 
 void hlr_host_free(hlr_host_hmatrix *hm);
 
+/* Checkpoint (no counterpart in the paper): write a built matrix to the file `path` so that a
+ * large construction runs once, and read it back. The file holds a versioned header, n, eps,
+ * the permutation, every block's ranges, kind, rank and FP64 data (D, or W, sigma, X), and a
+ * 64-bit FNV-1a hash of all preceding bytes. hlr_host_load returns a matrix owned by the
+ * library (free with hlr_host_free) that describes, uploads and computes exactly like the
+ * saved one. Errors: HLR_ERR_INVALID (null argument, unreadable or unwritable file, wrong
+ * magic or version, checksum mismatch, truncated or malformed contents). Host only. */
+int hlr_host_save(const hlr_host_hmatrix *hm, const char *path);
+int hlr_host_load(const char *path, hlr_host_hmatrix **out);
+
 #ifdef __cplusplus
 }
 #endif

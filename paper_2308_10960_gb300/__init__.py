@@ -10,6 +10,7 @@ PyTorch provides device memory and streams only.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -20,7 +21,8 @@ from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ERR_INVALID, H
 __all__ = [
     "HlrError", "DeviceHMatrix", "HostHMatrix", "upload", "build_kernel_hmatrix", "afl_encode",
     "afl_decode_device", "matvec_batched", "HLR_ACC_FP32", "HLR_ACC_FP64", "HLR_FMT_AFL_APLR", "HLR_FMT_FP64",
-    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code", "encode",
+    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code", "encode", "encode_device", "unit_arrays",
+    "load_host_hmatrix",
 ]
 
 _ACC = {"fp32": HLR_ACC_FP32, "fp64": HLR_ACC_FP64, HLR_ACC_FP32: HLR_ACC_FP32, HLR_ACC_FP64: HLR_ACC_FP64}
@@ -261,6 +263,10 @@ class HostHMatrix:
                 if k else np.zeros((d.ncols, 0))
         return b
 
+    def save(self, path: str):
+        """Checkpoint the matrix to `path` (hlr_host_save); read it back with load_host_hmatrix."""
+        B.check(B.lib.hlr_host_save(C.c_void_p(self.ptr), os.fsencode(path)))
+
     def unit_arrays(self, fmt: str = "afl", eps: float | None = None):
         """The matrix's units in upload order as (values, offsets, precisions): see
         ``unit_arrays``; reads the blocks in place (no per-block copies)."""
@@ -318,6 +324,13 @@ def build_kernel_hmatrix(points: np.ndarray, kernel: str, eps: float, scale: flo
     out = C.c_void_p(0)
     B.check(B.lib.hlr_build(C.byref(prob), C.byref(out)))
     return HostHMatrix(out.value, P)
+
+
+def load_host_hmatrix(path: str) -> HostHMatrix:
+    """A matrix saved by HostHMatrix.save (hlr_host_load: checked against its version and hash)."""
+    out = C.c_void_p(0)
+    B.check(B.lib.hlr_host_load(os.fsencode(path), C.byref(out)))
+    return HostHMatrix(out.value, None)
 
 
 def encode(a: np.ndarray, u: float, fmt: str = "afl"):

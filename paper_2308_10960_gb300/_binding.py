@@ -104,6 +104,8 @@ SIGNATURES = [
     ("hlr_build", C.c_int, [C.POINTER(KernelProblem), C.POINTER(C.c_void_p)]),
     ("hlr_host_describe", C.c_int, [C.c_void_p, C.POINTER(HMatrixDesc)]),
     ("hlr_host_free", None, [C.c_void_p]),
+    ("hlr_host_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("hlr_host_load", C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
 ]
 
 

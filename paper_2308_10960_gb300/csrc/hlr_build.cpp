@@ -16,9 +16,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "hlr_internal.h"
@@ -412,6 +414,26 @@ void recompress(int64_t m, int64_t n, const std::vector<std::vector<double>> &us
 
 }  // namespace
 
+// block descriptors pointing into the matrix's own arrays
+static void fill_descs(hlr_host_hmatrix &H) {
+  const int64_t nb = int64_t(H.blocks.size());
+  H.descs.resize(nb);
+  for (int64_t b = 0; b < nb; ++b) {
+    const auto &B = H.blocks[b];
+    hlr_block_desc &d = H.descs[b];
+    d.row0 = B.row0;
+    d.nrows = B.nrows;
+    d.col0 = B.col0;
+    d.ncols = B.ncols;
+    d.kind = B.kind;
+    d.rank = B.rank;
+    d.D = B.D.empty() ? nullptr : B.D.data();
+    d.W = B.W.empty() ? nullptr : B.W.data();
+    d.sigma = B.S.empty() ? nullptr : B.S.data();
+    d.X = B.X.empty() ? nullptr : B.X.data();
+  }
+}
+
 extern "C" int hlr_build(const hlr_kernel_problem *p, hlr_host_hmatrix **out) {
   if (!p || !out || !p->points) return set_error(HLR_ERR_INVALID, "hlr_build: null argument");
   *out = nullptr;
@@ -479,21 +501,7 @@ extern "C" int hlr_build(const hlr_kernel_problem *p, hlr_host_hmatrix **out) {
     }
   }
   H->perm = T.perm;
-  H->descs.resize(nb);
-  for (int64_t b = 0; b < nb; ++b) {
-    const auto &B = H->blocks[b];
-    hlr_block_desc &d = H->descs[b];
-    d.row0 = B.row0;
-    d.nrows = B.nrows;
-    d.col0 = B.col0;
-    d.ncols = B.ncols;
-    d.kind = B.kind;
-    d.rank = B.rank;
-    d.D = B.D.empty() ? nullptr : B.D.data();
-    d.W = B.W.empty() ? nullptr : B.W.data();
-    d.sigma = B.S.empty() ? nullptr : B.S.data();
-    d.X = B.X.empty() ? nullptr : B.X.data();
-  }
+  fill_descs(*H);
   *out = H.release();
   return HLR_OK;
 }
@@ -511,3 +519,154 @@ extern "C" int hlr_host_describe(const hlr_host_hmatrix *hm, hlr_hmatrix_desc *d
 }
 
 extern "C" void hlr_host_free(hlr_host_hmatrix *hm) { delete hm; }
+
+// ---- checkpoint: the FP64 host matrix in one file --------------------------------------------
+// Layout (little-endian): "HLRHMAT\0", u32 version (1), u32 0, i64 n, i64 nblocks, f64 eps,
+// i64 perm[n]; per block i64 row0, nrows, col0, ncols, i32 kind, i32 rank, then D (dense,
+// column-major nrows x ncols) or W (nrows x rank), sigma (rank), X (ncols x rank); last, the
+// FNV-1a 64-bit hash of every byte before it.
+namespace {
+constexpr char kMagic[8] = {'H', 'L', 'R', 'H', 'M', 'A', 'T', '\0'};
+constexpr uint32_t kVersion = 1;
+
+uint64_t fnv1a(const uint8_t *p, size_t n) {
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct Writer {
+  std::vector<uint8_t> buf;
+  template <typename T>
+  void put(const T &v) {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(&v);
+    buf.insert(buf.end(), p, p + sizeof(T));
+  }
+  void put_doubles(const std::vector<double> &v) {
+    const uint8_t *p = reinterpret_cast<const uint8_t *>(v.data());
+    buf.insert(buf.end(), p, p + 8 * v.size());
+  }
+};
+
+struct Reader {
+  const uint8_t *p;
+  size_t n, at = 0;
+  bool ok = true;
+  template <typename T>
+  T get() {
+    T v{};
+    if (at + sizeof(T) > n) {
+      ok = false;
+      return v;
+    }
+    std::memcpy(&v, p + at, sizeof(T));
+    at += sizeof(T);
+    return v;
+  }
+  bool get_doubles(std::vector<double> &v, uint64_t count) {
+    if (count > (n - at) / 8) return ok = false;
+    v.resize(size_t(count));
+    std::memcpy(v.data(), p + at, size_t(count) * 8);
+    at += size_t(count) * 8;
+    return true;
+  }
+};
+}  // namespace
+
+extern "C" int hlr_host_save(const hlr_host_hmatrix *hm, const char *path) {
+  if (!hm || !path) return set_error(HLR_ERR_INVALID, "hlr_host_save: null argument");
+  Writer w;
+  w.buf.insert(w.buf.end(), kMagic, kMagic + 8);
+  w.put(kVersion);
+  w.put(uint32_t(0));
+  w.put(int64_t(hm->n));
+  w.put(int64_t(hm->blocks.size()));
+  w.put(hm->eps);
+  for (int64_t v : hm->perm) w.put(v);
+  for (const auto &B : hm->blocks) {
+    w.put(B.row0);
+    w.put(B.nrows);
+    w.put(B.col0);
+    w.put(B.ncols);
+    w.put(int32_t(B.kind));
+    w.put(int32_t(B.rank));
+    if (B.kind == HLR_DENSE) {
+      w.put_doubles(B.D);
+    } else {
+      w.put_doubles(B.W);
+      w.put_doubles(B.S);
+      w.put_doubles(B.X);
+    }
+  }
+  w.put(fnv1a(w.buf.data(), w.buf.size()));
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: cannot open ") + path);
+  const size_t put = std::fwrite(w.buf.data(), 1, w.buf.size(), f);
+  const int cl = std::fclose(f);
+  if (put != w.buf.size() || cl != 0) return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: write failed: ") + path);
+  return HLR_OK;
+}
+
+extern "C" int hlr_host_load(const char *path, hlr_host_hmatrix **out) {
+  if (!path || !out) return set_error(HLR_ERR_INVALID, "hlr_host_load: null argument");
+  *out = nullptr;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return set_error(HLR_ERR_INVALID, std::string("hlr_host_load: cannot open ") + path);
+  std::vector<uint8_t> buf;
+  uint8_t chunk[1 << 16];
+  size_t got;
+  while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+  std::fclose(f);
+  if (buf.size() < 8 + 4 + 4 + 8 + 8 + 8 + 8 || std::memcmp(buf.data(), kMagic, 8) != 0)
+    return set_error(HLR_ERR_INVALID, "hlr_host_load: not a saved H-matrix");
+  const size_t body = buf.size() - 8;
+  uint64_t h;
+  std::memcpy(&h, buf.data() + body, 8);
+  if (h != fnv1a(buf.data(), body)) return set_error(HLR_ERR_INVALID, "hlr_host_load: checksum mismatch");
+  Reader r{buf.data(), body};
+  r.at = 8;
+  const uint32_t version = r.get<uint32_t>();
+  r.get<uint32_t>();
+  if (version != kVersion) return set_error(HLR_ERR_INVALID, "hlr_host_load: unsupported version");
+  auto H = std::make_unique<hlr_host_hmatrix>();
+  H->n = r.get<int64_t>();
+  const int64_t nb = r.get<int64_t>();
+  H->eps = r.get<double>();
+  if (!r.ok || H->n <= 0 || nb <= 0 || uint64_t(H->n) > (body - r.at) / 8 || uint64_t(nb) > (body - r.at) / 40)
+    return set_error(HLR_ERR_INVALID, "hlr_host_load: bad sizes");
+  H->perm.resize(size_t(H->n));
+  for (auto &v : H->perm) {
+    v = r.get<int64_t>();
+    if (v < 0 || v >= H->n) r.ok = false;
+  }
+  H->blocks.resize(size_t(nb));
+  for (auto &B : H->blocks) {
+    B.row0 = r.get<int64_t>();
+    B.nrows = r.get<int64_t>();
+    B.col0 = r.get<int64_t>();
+    B.ncols = r.get<int64_t>();
+    B.kind = r.get<int32_t>();
+    B.rank = r.get<int32_t>();
+    if (!r.ok || B.row0 < 0 || B.nrows <= 0 || B.col0 < 0 || B.ncols <= 0 || B.row0 > H->n - B.nrows ||
+        B.col0 > H->n - B.ncols || B.rank < 0 || (B.kind != HLR_DENSE && B.kind != HLR_LOWRANK) ||
+        (B.kind == HLR_DENSE && B.rank != 0)) {
+      r.ok = false;
+      break;
+    }
+    if (B.kind == HLR_DENSE) {
+      r.get_doubles(B.D, uint64_t(B.nrows) * uint64_t(B.ncols));
+    } else {
+      r.get_doubles(B.W, uint64_t(B.nrows) * uint64_t(B.rank));
+      r.get_doubles(B.S, uint64_t(B.rank));
+      r.get_doubles(B.X, uint64_t(B.ncols) * uint64_t(B.rank));
+    }
+    if (!r.ok) break;
+  }
+  if (!r.ok || r.at != body) return set_error(HLR_ERR_INVALID, "hlr_host_load: truncated or malformed file");
+  fill_descs(*H);
+  *out = H.release();
+  return HLR_OK;
+}

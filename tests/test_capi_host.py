@@ -237,3 +237,46 @@ def test_host_hmatrix_unit_arrays_match_block_copies():
                 assert np.array_equal(x, y)
     finally:
         Hh.free()
+
+
+def test_host_checkpoint_round_trip_and_corruption(tmp_path):
+    """hlr_host_save / hlr_host_load: the loaded matrix has the same permutation, eps, block
+    structure and bits; a flipped byte, a truncated file, another magic or version are refused."""
+    p = synth.laplace_problem(1500)
+    Hh = hg.build_kernel_hmatrix(p.points, "laplace", 1e-6, diag=p.params["diag"])
+    path = str(tmp_path / "m.hlr")
+    try:
+        Hh.save(path)
+        G = hg.load_host_hmatrix(path)
+        try:
+            assert G.n == Hh.n and G.eps == Hh.eps and np.array_equal(G.perm, Hh.perm)
+            assert np.array_equal(G.structure(), Hh.structure())
+            for i in range(Hh.structure().shape[0]):
+                a, b = Hh.block(i), G.block(i)
+                for k in ("D", "W", "S", "X"):
+                    if k in a:
+                        assert np.array_equal(np.asarray(a[k]).view(np.int64), np.asarray(b[k]).view(np.int64))
+            va, oa, ua = Hh.unit_arrays()
+            vb, ob, ub = G.unit_arrays()
+            assert np.array_equal(va, vb) and np.array_equal(oa, ob) and np.array_equal(ua, ub)
+        finally:
+            G.free()
+    finally:
+        Hh.free()
+    raw = open(path, "rb").read()
+    bad = []
+    flipped = bytearray(raw)
+    flipped[len(raw) // 2] ^= 0x10
+    bad.append(bytes(flipped))
+    bad.append(raw[:-100])
+    bad.append(b"XXXXXXXX" + raw[8:])
+    ver = bytearray(raw)
+    ver[8] = 2
+    bad.append(bytes(ver))
+    for k, data in enumerate(bad):
+        q = str(tmp_path / f"bad{k}.hlr")
+        open(q, "wb").write(data)
+        with pytest.raises(hg.HlrError):
+            hg.load_host_hmatrix(q)
+    with pytest.raises(hg.HlrError):
+        hg.load_host_hmatrix(str(tmp_path / "missing.hlr"))
