@@ -90,6 +90,60 @@ def rows_of(C: hm.CHMatrix, x: np.ndarray, rows: np.ndarray, y: np.ndarray | Non
     return np.array(out)
 
 
+def rows_exact(C: hm.CHMatrix, x: np.ndarray, rows: np.ndarray, y: np.ndarray | None = None) -> np.ndarray:
+    """Entries ``rows`` (original indices) of y_in + A~ x with the terms of ``rows_of`` (each
+    block's contribution to a row an exactly rounded sum, then all contributions and y_in in
+    one exactly rounded sum), but every block that covers one of the rows is decoded, and its
+    t_b = Sigma_b (X~_b^T x|sigma) formed, only once. C may hold just the blocks that cover the
+    rows."""
+    inv = np.empty(C.n, dtype=np.int64)
+    inv[C.perm] = np.arange(C.n)
+    xp = np.asarray(x, dtype=np.float64)[C.perm]
+    rows = np.asarray(rows, dtype=np.int64)
+    pos = inv[rows]
+    order = np.argsort(pos, kind="stable")
+    spos = pos[order]
+    terms = [[0.0 if y is None else float(y[i])] for i in rows]
+    for b in C.blocks:
+        lo = int(np.searchsorted(spos, b.row0, side="left"))
+        hi = int(np.searchsorted(spos, b.row0 + b.nrows, side="left"))
+        if lo == hi:
+            continue
+        xs = xp[b.col0:b.col0 + b.ncols]
+        if b.kind == hm.DENSE:
+            D = hm.decode_block(b)
+            for q in order[lo:hi]:
+                terms[q].append(math.fsum(D[pos[q] - b.row0] * xs))
+        elif b.rank:
+            W, S, X = hm.decode_block(b)
+            t = S * np.array([math.fsum(X[:, k] * xs) for k in range(b.rank)])
+            for q in order[lo:hi]:
+                terms[q].append(math.fsum(W[pos[q] - b.row0] * t))
+    return np.array([math.fsum(tq) for tq in terms])
+
+
+def abs_rows(C: hm.CHMatrix, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """sum_j |A~_ij| |x_j| for the original indices ``rows`` (the scale of componentwise
+    error bounds); C may hold just the blocks that cover the rows."""
+    inv = np.empty(C.n, dtype=np.int64)
+    inv[C.perm] = np.arange(C.n)
+    xa = np.abs(np.asarray(x, dtype=np.float64))[C.perm]
+    pos = inv[np.asarray(rows, dtype=np.int64)]
+    out = np.zeros(pos.size)
+    for b in C.blocks:
+        sel = np.nonzero((pos >= b.row0) & (pos < b.row0 + b.nrows))[0]
+        if sel.size == 0:
+            continue
+        xs = xa[b.col0:b.col0 + b.ncols]
+        r = pos[sel] - b.row0
+        if b.kind == hm.DENSE:
+            out[sel] += np.abs(hm.decode_block(b)[r]) @ xs
+        elif b.rank:
+            W, S, X = hm.decode_block(b)
+            out[sel] += np.abs((W[r] * S) @ X.T) @ xs
+    return out
+
+
 def dense_rows(problem, x: np.ndarray, rows: np.ndarray) -> np.ndarray:
     """(A x)[rows] by direct kernel evaluation of the full rows (the plain definition)."""
     x = np.asarray(x, dtype=np.float64)

@@ -66,3 +66,26 @@ def test_cg_matches_direct_solution():
     xc, info = scipy_sparse.cg(At, b, rtol=1e-10, maxiter=2000)
     assert info == 0
     assert np.linalg.norm(x - xc) / np.linalg.norm(xc) <= kappa * 1e-10 * 10
+
+
+def test_rows_exact_and_abs_rows_against_full_product(exp2d_case):
+    """rows_exact gives the full product's entries bit for bit (the same exactly rounded sums),
+    also from the sub-list of blocks that cover the rows; abs_rows equals |A~| |x| from the
+    decoded dense matrix."""
+    p, H, C = exp2d_case
+    x = synth.rhs(p.n, 3)
+    y0 = np.random.default_rng(4).standard_normal(p.n)
+    full = mv.matvec(C, x, y0)
+    rows = np.sort(np.random.default_rng(5).choice(p.n, size=96, replace=False))
+    got = mv.rows_exact(C, x, rows, y0)
+    assert np.array_equal(got.view(np.int64), full[rows].view(np.int64))
+    inv = np.empty(p.n, dtype=np.int64)
+    inv[C.perm] = np.arange(p.n)
+    pos = inv[rows]
+    sub = hm.CHMatrix(C.n, C.perm, [b for b in C.blocks if np.any((pos >= b.row0) & (pos < b.row0 + b.nrows))], C.eps)
+    assert len(sub.blocks) < len(C.blocks)
+    got2 = mv.rows_exact(sub, x, rows, y0)
+    assert np.array_equal(got2.view(np.int64), got.view(np.int64))
+    At = hm.to_dense(C)
+    ref = np.abs(At[rows]) @ np.abs(x)
+    np.testing.assert_allclose(mv.abs_rows(sub, x, rows), ref, rtol=1e-13)
