@@ -65,6 +65,13 @@ extern "C" {
                               kernels, whose result for a column does not depend on the other
                               columns or requests it is launched with */
 
+/* OR-ed into the flags of hlr_matvec, hlr_matvec_host, hlr_matvec_batched and hlr_solve_cg:
+ * the persistent product kernels take about eighths/8 of their CTA slots (1..7; 0 or 8 = all),
+ * each CTA then walking the work lists of several slots, so that work running concurrently on
+ * other streams keeps the rest of every SM (e.g. served solves beside served products). The
+ * result does not depend on it. */
+#define HLR_SM_SHARE(eighths) ((eighths) << 16)
+
 typedef uint64_t hlr_handle; /* 0 is never a valid handle */
 
 /* One leaf block b = (tau, sigma) of the block tree (Def. 2.2) in CLUSTER order: rows
@@ -104,6 +111,10 @@ typedef struct {
  *  leaf     rows of a phase-2 task: 32 or 64 (default; longer leaves are split);
  *  piece_kb bytes of a piece, in KiB: 4 .. 16 (default 16). */
 #define HLR_TUNING(sub_log2, leaf_log2, piece_kb) ((sub_log2) | ((leaf_log2) << 4) | ((piece_kb) << 8))
+/* OR-ed into hlr_hmatrix_desc.tuning (any format): keep the decode map of hlr_decode_units
+ * whatever the matrix size (it costs 24 bytes of host memory per column slice), e.g. to check
+ * the stored codes of a large matrix against an independent decoder. */
+#define HLR_DECODE_MAP (1 << 16)
 
 /* Sizes of an uploaded matrix (hlr_get_info). Byte counts exclude alignment padding. */
 typedef struct {
@@ -120,8 +131,10 @@ typedef struct {
                                  singular value (Sigma read, t written) + 4n (x, once)        */
   uint64_t phase2_bytes;      /* phase 2: W and dense streams + their headers + 8 per singular
                                  value (t) + 8n (x, once) + 16n (y) + 8n (perm)              */
-  int64_t launches;           /* kernels one hlr_matvec launches (permute, phase 1, combine of
-                                 split blocks, phase 2; a phase without work is not launched) */
+  int64_t launches;           /* kernels one hlr_matvec with HLR_ACC_FP32 launches (permute,
+                                 phase 1, combine of split blocks, phase 2 and, for the AFL and
+                                 AFLP formats, the scatter of its row totals into y; a phase
+                                 without work is not launched) */
 } hlr_info;
 
 /* Encode the matrix (AFL-APLR or FP64), build the work lists of the product (blocks grouped by
@@ -159,7 +172,9 @@ int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
                        double *const *Y_dev, const int64_t *ldy, int flags, void *cuda_stream);
 
 /* Unpreconditioned conjugate gradients for A~ x = b (A~ symmetric positive definite), with
- * x_dev as initial guess on entry and the solution on return. Inner products (reduced in a
+ * x_dev as initial guess on entry and the solution on return. The paper defines no solver: CG
+ * is here as the repeated application of the product of Section 5.4 that a served solve
+ * request needs (the textbook Hestenes-Stiefel iteration), not as a passage of the paper. Inner products (reduced in a
  * fixed order) and vector updates are FP64. flags:
  *  HLR_ACC_FP64: CG with FP64-accumulation products, stopped when the recursive residual has
  *                ||r|| <= rtol ||b||;
@@ -167,7 +182,8 @@ int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
  *                product, the correction A~ d = r is solved by CG with the FP32-accumulation
  *                product to a relative 1e-3 (or what the last step needs), x += d, until the
  *                TRUE residual has ||b - A~ x|| <= rtol ||b||.
- * Synchronous (one small device-to-host read per iteration). Returns *iters (CG iterations,
+ * Synchronous: iterations are launched eight at a time and the host reads the residual after
+ * each group (a converged iterate is left unchanged by the rest of its group). Returns *iters (CG iterations,
  * all corrections together) and *relres, the relative TRUE residual ||b - A~ x|| / ||b|| of
  * the returned x (FP64 product). HLR_ERR_NOCONV when maxit is reached. Workspace of 5n doubles
  * is allocated per handle on the first solve. */
@@ -180,6 +196,15 @@ int hlr_solve_cg(hlr_handle h, const double *b_dev, double *x_dev, double rtol, 
  * a shared-memory slot gives up after about 2 s. */
 int hlr_check(hlr_handle h, void *cuda_stream);
 
+/* Failure-detection self-test (no counterpart in the paper): launches on cuda_stream one small
+ * kernel that waits, with the same bounded wait as the product kernels, on a shared-memory
+ * barrier that nothing ever completes, and gives up after `cycles` SM clock cycles (1000 ..
+ * 2^31, about 1 s at most). It then records the expired wait in h's status word, so that the
+ * next hlr_check(h) returns HLR_ERR_TIMEOUT and clears it. Nothing faults or hangs: the
+ * context, the handle and its data stay usable. Errors: HLR_ERR_INVALID (unknown handle,
+ * cycles out of range), HLR_ERR_CUDA (launch). */
+int hlr_selftest_wait(hlr_handle h, int64_t cycles, void *cuda_stream);
+
 /* Release the device arena of h (synchronises the device first). */
 int hlr_free(hlr_handle h);
 
@@ -191,7 +216,8 @@ int hlr_get_info(hlr_handle h, hlr_info *out);
 
 /* Per-kernel device time of the products launched with HLR_PROFILE since the previous read:
  * kernel_ms[0] = x permutation, [1] = phase 1 (t = Sigma X~^T x), [2] = phase 2 (y += W~ t, D~ x),
- * summed over *calls products. Waits for the recorded events. At most 4096 products are kept
+ * [3] = the scatter of phase 2's row totals into y (0 for paths that update y in phase 2),
+ * summed over *calls products (kernel_ms holds 4 values). Waits for the recorded events. At most 4096 products are kept
  * between reads; later ones are not recorded. */
 int hlr_profile_read(hlr_handle h, double *kernel_ms, int *calls);
 
@@ -236,6 +262,22 @@ int hlr_encode_device(int32_t fmt, int64_t nunits, const int64_t *off_dev, int64
                       const double *u_dev, double *m_min_dev, int32_t *e_dev, int32_t *m_dev, int64_t *out_off_dev,
                       uint8_t *out_dev, size_t cap, void *cuda_stream);
 
+/* The units of a matrix as hlr_upload forms and encodes them (Section 3.3), in upload order:
+ * a dense leaf is one unit, its column-major values, at the precision eps of Eq. 1 (for
+ * HLR_FMT_MP 2^-60, which selects FP64); a lowrank leaf of rank k > 0 gives its k W columns,
+ * then its k X columns, column i of either at the adaptive precision
+ * u_i = eps sigma_0 / sigma_i (delta = eps sigma_0, the truncation threshold of Eq. 1). These
+ * are the inputs hlr_encode / hlr_encode_device take for a unit. Host only.
+ *   *nunits, *nvalues (out): the number of units and of their values (always set);
+ *   off[nunits + 1] (out, optional): unit u holds values off[u] .. off[u+1]);
+ *   prec[nunits]    (out, optional): the precision of unit u;
+ *   values[nvalues] (out, optional): the values of all units, concatenated.
+ * Pass NULL outputs to query the sizes first. Errors: HLR_ERR_INVALID (null descriptor, bad
+ * rank or sigma, eps outside (0, 1) for a compressed format), HLR_ERR_OOM (cap_units below
+ * nunits + 1 with off, below nunits with prec, or cap_values below nvalues with values). */
+int hlr_unit_list(const hlr_hmatrix_desc *d, int64_t *off, double *prec, double *values, int64_t cap_units,
+                  int64_t cap_values, int64_t *nunits, int64_t *nvalues);
+
 /* Decode one AFL stream on the GPU into n FP64 values, bit-exact IEEE round-to-nearest
  * ((v - 1) * m_min without contraction, Section 3.2). stream_dev must be 16-byte aligned and
  * hold ceil(n (1+e+m) / 8) bytes rounded up to 16. */
@@ -245,8 +287,9 @@ int hlr_afl_decode_device(const uint8_t *stream_dev, int64_t n, double m_min, in
 /* Decode every unit of an uploaded matrix to FP64 on the GPU, concatenated in unit order
  * (per block in block order: dense -> its column-major values; lowrank -> W columns then X
  * columns). cap is the capacity of out_dev in doubles (>= hlr_info.values). Available for
- * matrices of at most 2^26 stored values (HLR_ERR_UNSUPPORTED above); allocates a temporary
- * device map and synchronises cuda_stream. */
+ * matrices of at most 2^26 stored values, or uploaded with HLR_DECODE_MAP in their tuning
+ * (HLR_ERR_UNSUPPORTED otherwise); allocates a temporary device map and synchronises
+ * cuda_stream. */
 int hlr_decode_units(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stream);
 
 /* The paper has no counterpart of this call: it is hlr_decode_units for callers that must not

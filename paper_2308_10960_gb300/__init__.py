@@ -117,17 +117,18 @@ class DeviceHMatrix:
         self.info = inf.as_dict()
         self.n = int(self.info["n"])
 
-    def matvec(self, x, y, acc="fp32", stream=None, profile=False):
-        """y += A~ x (both contiguous float64 CUDA tensors of length n, original order)."""
-        flags = _ACC[acc] | (B.HLR_PROFILE if profile else 0)
+    def matvec(self, x, y, acc="fp32", stream=None, profile=False, sm_share: int = 0):
+        """y += A~ x (both contiguous float64 CUDA tensors of length n, original order).
+        sm_share: 1..7 eighths of the persistent kernels' CTA slots (HLR_SM_SHARE; 0 = all)."""
+        flags = _ACC[acc] | (B.HLR_PROFILE if profile else 0) | (int(sm_share) << 16)
         B.check(B.lib.hlr_matvec(C.c_uint64(self.handle), _dev_ptr(x, self.n), _dev_ptr(y, self.n),
                                  flags, _stream_ptr(stream)))
         return y
 
     def profile_read(self):
-        """(per-kernel milliseconds [permute, phase1, phase2] summed, number of products) of the
-        products launched with profile=True since the previous read."""
-        ms = (C.c_double * 3)()
+        """(per-kernel milliseconds [permute, phase1, phase2, scatter] summed, number of products)
+        of the products launched with profile=True since the previous read."""
+        ms = (C.c_double * 4)()
         calls = C.c_int(0)
         B.check(B.lib.hlr_profile_read(C.c_uint64(self.handle), ms, C.byref(calls)))
         return list(ms), calls.value
@@ -140,12 +141,14 @@ class DeviceHMatrix:
         B.check(B.lib.hlr_matvec_host(C.c_uint64(self.handle), xp, yp, _ACC[acc], _stream_ptr(stream)))
         return y
 
-    def solve_cg(self, b, x, rtol=1e-8, maxit=1000, acc="fp64", stream=None, raise_noconv=True):
-        """Solve A~ x = b by CG (x holds the initial guess). Returns (iterations, true rel. residual)."""
+    def solve_cg(self, b, x, rtol=1e-8, maxit=1000, acc="fp64", stream=None, raise_noconv=True, sm_share: int = 0):
+        """Solve A~ x = b by CG (x holds the initial guess). Returns (iterations, true rel. residual).
+        sm_share: 1..7 eighths of the product kernels' CTA slots (HLR_SM_SHARE; 0 = all)."""
         it = C.c_int(0)
         rel = C.c_double(0.0)
         rc = B.lib.hlr_solve_cg(C.c_uint64(self.handle), _dev_ptr(b, self.n), _dev_ptr(x, self.n), float(rtol),
-                                int(maxit), _ACC[acc], _stream_ptr(stream), C.byref(it), C.byref(rel))
+                                int(maxit), _ACC[acc] | (int(sm_share) << 16), _stream_ptr(stream), C.byref(it),
+                                C.byref(rel))
         if rc == HLR_ERR_NOCONV and not raise_noconv:
             return it.value, rel.value
         B.check(rc)
@@ -167,6 +170,12 @@ class DeviceHMatrix:
     def check(self, stream=None):
         """Wait for the stream; raise HlrError(HLR_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
         B.check(B.lib.hlr_check(C.c_uint64(self.handle), _stream_ptr(stream)))
+
+    def selftest_wait(self, cycles: int = 2_000_000, stream=None):
+        """Launch the failure-detection self-test (hlr_selftest_wait): a bounded device wait
+        that cannot succeed and gives up after `cycles` clock cycles; the next check() raises
+        HlrError(HLR_ERR_TIMEOUT)."""
+        B.check(B.lib.hlr_selftest_wait(C.c_uint64(self.handle), int(cycles), _stream_ptr(stream)))
 
     def free(self):
         if self.handle:
@@ -202,7 +211,7 @@ def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None, tuning: int
     return DeviceHMatrix(h.value)
 
 
-def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None, multi=False):
+def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None, multi=False, sm_share: int = 0):
     """Y_q += A~_q X_q for every request q (X_q, Y_q: n_q x r_q column-major float64 CUDA tensors,
     i.e. tensors of shape (r_q, n_q) in row-major memory, or 1-D of length n_q). multi=True
     (FP32 only) runs single columns through the multi-RHS kernels too, so that a column's result
@@ -221,7 +230,7 @@ def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None, multi=False):
         yp[i] = _dev_ptr(Y, m.n * r)
         lx[i] = m.n
         ly[i] = m.n
-    flags = _ACC[acc] | (B.HLR_MULTI if multi else 0)
+    flags = _ACC[acc] | (B.HLR_MULTI if multi else 0) | (int(sm_share) << 16)
     B.check(B.lib.hlr_matvec_batched(q, hs, nr, xp, lx, yp, ly, flags, _stream_ptr(stream)))
 
 
@@ -263,31 +272,60 @@ class HostHMatrix:
                 if k else np.zeros((d.ncols, 0))
         return b
 
+    def block_views(self):
+        """Every block as a dict like ``block(i)`` but with numpy views of the library's own
+        arrays (no copies; valid until free())."""
+        out = []
+        for i in range(self.desc.nblocks):
+            d = self.desc.blocks[i]
+            b = {"row0": d.row0, "nrows": d.nrows, "col0": d.col0, "ncols": d.ncols, "kind": d.kind}
+            if d.kind == HLR_DENSE:
+                b["D"] = np.ctypeslib.as_array(d.D, shape=(d.nrows * d.ncols,)).reshape(d.nrows, d.ncols, order="F")
+            else:
+                k = d.rank
+                if k:
+                    b["S"] = np.ctypeslib.as_array(d.sigma, shape=(k,))
+                    b["W"] = np.ctypeslib.as_array(d.W, shape=(d.nrows * k,)).reshape(d.nrows, k, order="F")
+                    b["X"] = np.ctypeslib.as_array(d.X, shape=(d.ncols * k,)).reshape(d.ncols, k, order="F")
+                else:
+                    b["S"] = np.zeros(0)
+            out.append(b)
+        return out
+
     def save(self, path: str):
         """Checkpoint the matrix to `path` (hlr_host_save); read it back with load_host_hmatrix."""
         B.check(B.lib.hlr_host_save(C.c_void_p(self.ptr), os.fsencode(path)))
 
     def unit_arrays(self, fmt: str = "afl", eps: float | None = None):
         """The matrix's units in upload order as (values, offsets, precisions): see
-        ``unit_arrays``; reads the blocks in place (no per-block copies)."""
-        def views():
-            for i in range(self.desc.nblocks):
-                d = self.desc.blocks[i]
-                if d.kind == HLR_DENSE:
-                    yield {"kind": d.kind, "D": np.ctypeslib.as_array(d.D, shape=(d.nrows * d.ncols,))}
-                elif d.rank > 0:
-                    k = d.rank
-                    yield {"kind": d.kind, "S": np.ctypeslib.as_array(d.sigma, shape=(k,)),
-                           "W": np.ctypeslib.as_array(d.W, shape=(d.nrows * k,)).reshape(d.nrows, k, order="F"),
-                           "X": np.ctypeslib.as_array(d.X, shape=(d.ncols * k,)).reshape(d.ncols, k, order="F")}
-        return unit_arrays(views(), self.eps if eps is None else float(eps), fmt)
-
-    def upload(self, fmt="afl", eps: float | None = None, stream=None, tuning: int = 0) -> DeviceHMatrix:
-        """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU. tuning:
-        work layout of the AFL kernels (``tuning_code``; 0 = default)."""
+        ``unit_arrays`` (hlr_unit_list over the library's own blocks)."""
         self.desc.format = _FMT[fmt]
         self.desc.eps = self.eps if eps is None else float(eps)
-        self.desc.tuning = int(tuning)
+        return _unit_list(self.desc)
+
+    def unit_offsets(self, fmt: str = "afl", eps: float | None = None):
+        """(offsets, precisions) of the matrix's units in upload order (hlr_unit_list without the
+        values): unit u holds the values offsets[u] .. offsets[u+1] of the unit order that
+        DeviceHMatrix.decode_units writes."""
+        self.desc.format = _FMT[fmt]
+        self.desc.eps = self.eps if eps is None else float(eps)
+        nu = C.c_int64(0)
+        nv = C.c_int64(0)
+        B.check(B.lib.hlr_unit_list(C.byref(self.desc), None, None, None, 0, 0, C.byref(nu), C.byref(nv)))
+        off = np.zeros(nu.value + 1, dtype=np.int64)
+        prec = np.zeros(nu.value, dtype=np.float64)
+        B.check(B.lib.hlr_unit_list(C.byref(self.desc), off.ctypes.data, prec.ctypes.data, None, nu.value + 1, 0,
+                                    C.byref(nu), C.byref(nv)))
+        return off, prec
+
+    def upload(self, fmt="afl", eps: float | None = None, stream=None, tuning: int = 0,
+               decode_map: bool = False) -> DeviceHMatrix:
+        """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU. tuning:
+        work layout of the AFL kernels (``tuning_code``; 0 = default); decode_map: keep the map
+        of decode_units whatever the size (HLR_DECODE_MAP)."""
+        self.desc.format = _FMT[fmt]
+        self.desc.eps = self.eps if eps is None else float(eps)
+        self.desc.tuning = int(tuning) | (B.HLR_DECODE_MAP if decode_map else 0)
         h = C.c_uint64(0)
         nbytes = C.c_size_t(0)
         B.check(B.lib.hlr_upload(C.byref(self.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))
@@ -374,34 +412,29 @@ def encode_device(values, offsets, precisions, fmt: str = "afl", stream=None):
     return m_min, e, m, out_off, out
 
 
+def _unit_list(desc):
+    nu = C.c_int64(0)
+    nv = C.c_int64(0)
+    B.check(B.lib.hlr_unit_list(C.byref(desc), None, None, None, 0, 0, C.byref(nu), C.byref(nv)))
+    off = np.zeros(nu.value + 1, dtype=np.int64)
+    prec = np.zeros(nu.value, dtype=np.float64)
+    vals = np.zeros(nv.value, dtype=np.float64)
+    B.check(B.lib.hlr_unit_list(C.byref(desc), off.ctypes.data, prec.ctypes.data, vals.ctypes.data, nu.value + 1,
+                                nv.value, C.byref(nu), C.byref(nv)))
+    return vals, off, prec
+
+
 def unit_arrays(blocks, eps: float, fmt: str = "afl"):
-    """Host: the units of a block list in upload order (dense leaf: its column-major values;
-    lowrank block: W columns, then X columns) as (values, offsets, precisions) numpy arrays,
-    with the precisions upload gives them (dense eps, lowrank column i eps sigma_0 / sigma_i;
-    MP dense leaves 2^-60, i.e. FP64)."""
-    vals, lens, prec = [], [], []
+    """The units of a block list (dicts as for ``upload``) in upload order as (values, offsets,
+    precisions) numpy arrays: dense leaf -> its column-major values, lowrank block -> W
+    columns, then X columns; each unit's precision is the one upload gives it (hlr_unit_list:
+    dense eps, lowrank column i eps sigma_0 / sigma_i, MP dense leaves FP64)."""
+    blocks = list(blocks)
+    n = 0
     for b in blocks:
-        if b["kind"] == HLR_DENSE:
-            D = np.asarray(b["D"], dtype=np.float64)
-            vals.append(D.ravel(order="F") if D.ndim == 2 else D)
-            lens.append(D.size)
-            prec.append(2.0 ** -60 if fmt == "mp" else eps)
-        else:
-            S = np.asarray(b["S"], dtype=np.float64)
-            k = S.size
-            if k == 0:
-                continue
-            W = np.asarray(b["W"], dtype=np.float64)
-            X = np.asarray(b["X"], dtype=np.float64)
-            u = (eps * S[0]) / S
-            vals += [W.ravel(order="F"), X.ravel(order="F")]
-            lens += [W.shape[0]] * k + [X.shape[0]] * k
-            prec += [u, u]
-    off = np.zeros(len(lens) + 1, dtype=np.int64)
-    np.cumsum(lens, out=off[1:])
-    v = np.concatenate(vals) if vals else np.zeros(0)
-    pr = np.concatenate([np.atleast_1d(np.asarray(q, dtype=np.float64)) for q in prec]) if prec else np.zeros(0)
-    return v, off, pr
+        n = max(n, int(b["row0"]) + int(b["nrows"]), int(b["col0"]) + int(b["ncols"]))
+    db = _DescBuilder(n, None, blocks, eps, _FMT[fmt])
+    return _unit_list(db.desc)
 
 
 def afl_encode(a: np.ndarray, u: float):

@@ -34,6 +34,7 @@ HLR_ACC_FP64 = 0
 HLR_ACC_FP32 = 1
 HLR_PROFILE = 0x100
 HLR_MULTI = 0x200
+HLR_DECODE_MAP = 1 << 16
 HLR_KERNEL_EXP = 1
 HLR_KERNEL_LAPLACE = 2
 HLR_KERNEL_MATERN15 = 3
@@ -87,6 +88,7 @@ SIGNATURES = [
     ("hlr_solve_cg", C.c_int, [C.c_uint64, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("hlr_check", C.c_int, [C.c_uint64, C.c_void_p]),
+    ("hlr_selftest_wait", C.c_int, [C.c_uint64, C.c_int64, C.c_void_p]),
     ("hlr_free", C.c_int, [C.c_uint64]),
     ("hlr_last_error", C.c_char_p, []),
     ("hlr_get_info", C.c_int, [C.c_uint64, C.POINTER(Info)]),
@@ -101,6 +103,8 @@ SIGNATURES = [
                                         C.c_void_p]),
     ("hlr_decode_units", C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
     ("hlr_decode_units_static", C.c_int, [C.c_uint64, C.c_void_p, C.c_int64, C.c_void_p]),
+    ("hlr_unit_list", C.c_int, [C.POINTER(HMatrixDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     ("hlr_build", C.c_int, [C.POINTER(KernelProblem), C.POINTER(C.c_void_p)]),
     ("hlr_host_describe", C.c_int, [C.c_void_p, C.POINTER(HMatrixDesc)]),
     ("hlr_host_free", None, [C.c_void_p]),

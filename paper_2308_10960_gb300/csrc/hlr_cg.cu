@@ -15,7 +15,8 @@ namespace {
 constexpr int kDotBlocks = 608;   // fixed grid of the reductions: 4 x 152 SMs (order is fixed)
 constexpr int kDotThreads = 256;
 
-enum { S_RR = 0, S_PAP = 1, S_RRNEW = 2, S_BB = 3, S_TMP = 4, S_N = 8 };
+enum { S_RR = 0, S_PAP = 1, S_RRNEW = 2, S_BB = 3, S_TMP = 4, S_IT = 5, S_N = 8 };
+constexpr int kCheckEvery = 8;  // CG iterations launched between two reads of the residual by the host
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -58,11 +59,15 @@ __global__ void k_init(const double *__restrict__ b, double *__restrict__ r, dou
   }
 }
 
-// alpha = rr / pAp ; x += alpha p ; r -= alpha Ap ; partial of r.r
+// alpha = rr / pAp ; x += alpha p ; r -= alpha Ap ; partial of r.r. Once rr <= stop2 the iteration
+// has converged: alpha = 0 leaves x and r as they are (the host reads the residual only every
+// kCheckEvery iterations), and only unconverged iterations are counted in scal[S_IT].
 __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                            const double *__restrict__ Ap, const double *scal, int64_t n, double *partial) {
+                            const double *__restrict__ Ap, double *scal, int64_t n, double *partial, double stop2) {
   __shared__ double sh[kDotThreads / 32];
-  const double alpha = scal[S_RR] / scal[S_PAP];
+  const bool done = !(scal[S_RR] > stop2);
+  const double alpha = done ? 0.0 : scal[S_RR] / scal[S_PAP];
+  if (!done && blockIdx.x == 0 && threadIdx.x == 0) scal[S_IT] += 1.0;
   double v = 0.0;
   for (int64_t i = blockIdx.x * int64_t(kDotThreads) + threadIdx.x; i < n; i += int64_t(kDotBlocks) * kDotThreads) {
     x[i] = fma(alpha, p[i], x[i]);
@@ -74,10 +79,11 @@ __global__ void k_update_xr(double *__restrict__ x, double *__restrict__ r, cons
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// beta = rrnew / rr ; p = r + beta p ; Ap = 0 ; rr = rrnew
+// beta = rrnew / rr ; p = r + beta p ; Ap = 0
 __global__ void k_update_p(double *__restrict__ p, const double *__restrict__ r, double *__restrict__ Ap,
-                           double *scal, int64_t n) {
-  const double beta = scal[S_RRNEW] / scal[S_RR];
+                           double *scal, int64_t n, double stop2) {
+  // a converged iteration keeps p finite (beta = 0) whatever rr is
+  const double beta = !(scal[S_RR] > stop2) ? 0.0 : scal[S_RRNEW] / scal[S_RR];
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
     p[i] = fma(beta, p[i], r[i]);
     Ap[i] = 0.0;
@@ -129,6 +135,7 @@ struct Cg {
   CgWork W;
   int64_t n;
   cudaStream_t st;
+  int share;  // HLR_SM_SHARE bits of the products
   double h_scal[S_N];
 
   void dot(const double *a, const double *c, int slot) {
@@ -143,7 +150,7 @@ struct Cg {
   // ||rhs - A sol|| with the FP64-accumulation product; the residual is left in W.rt
   int true_residual(const double *rhs, const double *sol, double *norm) {
     int rc = ck(cudaMemsetAsync(W.rt, 0, 8 * size_t(n), st), "hlr_solve_cg");
-    if (!rc) rc = launch_matvec(H, sol, W.rt, HLR_ACC_FP64, st);
+    if (!rc) rc = launch_matvec(H, sol, W.rt, HLR_ACC_FP64 | share, st);
     if (rc) return rc;
     k_residual<<<2 * kDotBlocks, 256, 0, st>>>(rhs, W.rt, n);
     dot(W.rt, W.rt, S_TMP);
@@ -158,25 +165,34 @@ struct Cg {
     if (rc) return rc;
     if (zero_start) {
       if ((rc = ck(cudaMemsetAsync(sol, 0, 8 * size_t(n), st), "hlr_solve_cg"))) return rc;
-    } else if ((rc = launch_matvec(H, sol, W.Ap, acc, st))) {
+    } else if ((rc = launch_matvec(H, sol, W.Ap, acc | share, st))) {
       return rc;
     }
     k_init<<<2 * kDotBlocks, 256, 0, st>>>(rhs, W.r, W.p, W.Ap, n);
     dot(W.r, W.r, S_RR);
+    if ((rc = ck(cudaMemsetAsync(W.scal + S_IT, 0, sizeof(double), st), "hlr_solve_cg"))) return rc;
     if ((rc = fetch())) return rc;
     double rr = h_scal[S_RR];
-    int it = 0;
+    int launched = 0, it = 0;
     bool ok = std::sqrt(rr) <= stop;
-    while (!ok && it < maxit) {
-      if ((rc = launch_matvec(H, W.p, W.Ap, acc, st))) return rc;
-      dot(W.p, W.Ap, S_PAP);
-      k_update_xr<<<kDotBlocks, kDotThreads, 0, st>>>(sol, W.r, W.p, W.Ap, W.scal, n, W.partial);
-      k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + S_RRNEW);
-      k_update_p<<<2 * kDotBlocks, 256, 0, st>>>(W.p, W.r, W.Ap, W.scal, n);
-      k_copy_scalar<<<1, 1, 0, st>>>(W.scal, S_RR, S_RRNEW);
+    const double stop2 = stop * stop;
+    // iterations are launched kCheckEvery at a time without waiting; the device stops updating x
+    // once the residual has dropped below stop, so the few iterations launched after that change
+    // nothing and are not counted
+    while (!ok && launched < maxit) {
+      const int batch = std::min(kCheckEvery, maxit - launched);
+      for (int k = 0; k < batch; ++k) {
+        if ((rc = launch_matvec(H, W.p, W.Ap, acc | share, st))) return rc;
+        dot(W.p, W.Ap, S_PAP);
+        k_update_xr<<<kDotBlocks, kDotThreads, 0, st>>>(sol, W.r, W.p, W.Ap, W.scal, n, W.partial, stop2);
+        k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + S_RRNEW);
+        k_update_p<<<2 * kDotBlocks, 256, 0, st>>>(W.p, W.r, W.Ap, W.scal, n, stop2);
+        k_copy_scalar<<<1, 1, 0, st>>>(W.scal, S_RR, S_RRNEW);
+      }
+      launched += batch;
       if ((rc = fetch())) return rc;
       rr = h_scal[S_RR];
-      ++it;
+      it = int(h_scal[S_IT]);
       if (!std::isfinite(rr)) return set_error(HLR_ERR_NOCONV, "hlr_solve_cg: breakdown (non-finite residual)");
       ok = std::sqrt(rr) <= stop;
     }
@@ -202,7 +218,7 @@ int solve_cg(Handle &H, const double *b, double *x, double rtol, int maxit, int 
   const int64_t n = H.L.n;
   double *base = static_cast<double *>(ws);
   Cg cg{H, CgWork{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 5 * n + kDotBlocks},
-        n, st, {}};
+        n, st, flags & HLR_SM_SHARE(15), {}};
   cg.dot(b, b, S_BB);
   if ((rc = cg.fetch())) return rc;
   const double bnorm = std::sqrt(cg.h_scal[S_BB]);
@@ -210,7 +226,7 @@ int solve_cg(Handle &H, const double *b, double *x, double rtol, int maxit, int 
   double rnorm = 0.0;
   if (bnorm == 0.0) {
     if ((rc = cg.true_residual(b, x, &rnorm))) return rc;
-  } else if (flags == HLR_ACC_FP64) {
+  } else if ((flags & 0xff) == HLR_ACC_FP64) {
     int it = 0;
     bool conv = false;
     if ((rc = cg.run(b, x, false, rtol * bnorm, maxit, HLR_ACC_FP64, &it, &conv))) return rc;
@@ -246,7 +262,9 @@ extern "C" int hlr_solve_cg(hlr_handle h, const double *b, double *x, double rto
   Handle *H = lookup(h);
   if (!H) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: unknown handle");
   if (!b || !x || !(rtol > 0) || maxit < 0) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: bad arguments");
-  if (flags != HLR_ACC_FP64 && flags != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_solve_cg: bad flags");
+  const int acc = flags & ~HLR_SM_SHARE(15);
+  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags >> 16) & 15) > 8)
+    return set_error(HLR_ERR_INVALID, "hlr_solve_cg: bad flags");
   return solve_cg(*H, b, x, rtol, maxit, flags, stream, iters, relres);
 }
 
@@ -255,8 +273,9 @@ extern "C" int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *
                                   void *stream) {
   if (nreq < 0 || (nreq > 0 && (!h || !nrhs || !X || !ldx || !Y || !ldy)))
     return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad arguments");
-  const int acc = flags & ~HLR_MULTI;
-  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags & HLR_MULTI) && acc != HLR_ACC_FP32))
+  const int acc = flags & ~(HLR_MULTI | HLR_SM_SHARE(15));
+  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags & HLR_MULTI) && acc != HLR_ACC_FP32) ||
+      ((flags >> 16) & 15) > 8)
     return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: bad flags");
   for (int q = 0; q < nreq; ++q) {
     Handle *H = lookup(h[q]);

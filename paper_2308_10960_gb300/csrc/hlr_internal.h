@@ -162,6 +162,8 @@ struct DevLayout {
   double *tw64;              // [rank_sum + 8]  t_i m_min(W_i)
   float *tw32;               // [rank_sum + 8]
   double *partial;           // [part_total]
+  double *ysum;              // [n + 8] phase-2 row sums in cluster order (single-RHS AFL FP32
+                             // path), added into y by k_scatter
   const Combine *comb;       // [ncnt] columns of blocks with several phase-1 chunks
   uint32_t *status;          // [4] error words (0 = ok)
   double *xdev;              // [n] device copy of a host x (hlr_matvec_host)
@@ -194,6 +196,7 @@ struct Handle {
   int prof_n = 0;
 };
 constexpr int kProfileCap = 4096;
+constexpr int kProfileEv = 5;  // events per profiled product: around permute, phase 1, phase 2, scatter
 
 // Error reporting (thread-local message).
 int set_error(int code, const std::string &msg);
@@ -208,6 +211,7 @@ int launch_decode_units(const Handle &H, double *out, void *stream);
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out,
                          void *stream_);
 int profile_read(Handle &H, double *ms, int *calls);
+int launch_wait_expire(const Handle &H, long long cycles, void *stream);  // hlr_selftest_wait
 int ctas_per_phase(int device, int nct[2]);  // persistent grid sizes of the two product kernels
 
 // Host codec (hlr_codec.cpp).

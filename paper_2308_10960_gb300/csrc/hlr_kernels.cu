@@ -147,12 +147,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of parity `parity` to complete; false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+// Wait for the phase of parity `parity` to complete; false after `limit` clock cycles (~2 s
+// by default).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, long long limit = kWaitCycles) {
   if (mbar_try_wait(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(b, parity))
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -162,6 +163,7 @@ __device__ __forceinline__ void tma_load(void *dst, const void *src, uint32_t by
       : "memory");
 }
 __device__ __forceinline__ void bar_consumers() { asm volatile("bar.sync 1, %0;" ::"r"(kConsumers) : "memory"); }
+
 
 // ---------------------------------------------------------------------------------------------
 // Decoding
@@ -348,6 +350,33 @@ __device__ __forceinline__ const LaneHdr *lane_hdrs(const uint8_t *slot, const P
   return reinterpret_cast<const LaneHdr *>(slot + 16 + 32 * size_t(ph->nseg));
 }
 
+// ---------------------------------------------------------------------------------------------
+// Two codes per window. For AFL codes whose FP32 bit pattern can be built with integer operations
+// (w <= 31, m <= 23, e <= 7; the FP32 fast path of dec_mul_f32), two consecutive codes of a lane
+// column come from one funnel-shifted window: for w <= 16 a 32-bit window of two shared words,
+// else a 64-bit window of three, so a code costs one and a half shared loads or fewer.
+// ---------------------------------------------------------------------------------------------
+// shared-memory word at byte address a + OFF
+template <int OFF>
+__device__ __forceinline__ uint32_t lds_at(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.b32 %0, [%1+%2];" : "=r"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+// Codes 2p and 2p + 1 of a bank column (word k at col_s + 128 k) of width w, starting at bit
+// b = 2p w; each at bit 0 of its word (other bits above it).
+//  WIDE = false: w <= 16, one 32-bit window; WIDE = true: w <= 31, a 64-bit window.
+template <bool WIDE>
+__device__ __forceinline__ void code_pair(uint32_t col_s, uint32_t b, uint32_t w, uint32_t &c0, uint32_t &c1) {
+  const uint32_t a = col_s + ((b >> 5) << 7);
+  const uint32_t w0 = lds_at<0>(a), w1 = lds_at<128>(a);
+  c0 = __funnelshift_r(w0, w1, b);
+  if constexpr (WIDE)
+    c1 = __funnelshift_r(c0, __funnelshift_r(w1, lds_at<256>(a), b), w);
+  else
+    c1 = c0 >> w;
+}
+
 // Value r of a slice (FP32 / FP64 accumulation types) for the generic (wide) path.
 template <typename A>
 __device__ __forceinline__ A dec_at(const uint32_t *p, uint32_t bit, const ColDec &c) {
@@ -407,6 +436,20 @@ __global__ void k_permute_multi(const __grid_constant__ Jobs<NB> J) {
     float4 *dst = reinterpret_cast<float4 *>(jb.xp + p * kRB);
 #pragma unroll
     for (int q = 0; q < kRB / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  }
+}
+
+// y[perm[p]] += ysum[p] for every single-RHS product of the launch (blockIdx.y) whose phase 2
+// leaves its row totals in ysum (AFL value format), in cluster order, one update per row
+// (deterministic)
+template <int NB>
+__global__ void k_scatter(const __grid_constant__ Jobs<NB> J) {
+  const Job &jb = J.j[blockIdx.y];
+  const DevLayout &L = jb.L;
+  if (L.vfmt != VF_AFL) return;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < L.n; p += int64_t(gridDim.x) * blockDim.x) {
+    double *yp = jb.y + __ldg(L.perm + p);
+    *yp = *yp + L.ysum[p];
   }
 }
 
@@ -470,10 +513,16 @@ __device__ void producer(const Jobs<NB> &J, uint8_t *smem, uint64_t *full, uint6
   const int lane = threadIdx.x & 31;
   uint32_t i = 0, cur = 0;
   int m = 0;
-  for (; m < J.n; ++m) {
+  bool ok = true;
+  for (; m < J.n && ok; ++m) {
     const PhaseDev &P = J.j[m].L.ph[PH];
-    const uint32_t e0 = __ldg(P.cta_e0 + blockIdx.x), e1 = __ldg(P.cta_e0 + blockIdx.x + 1);
-    if (!produce<FMT, PH, R>(J.j[m].L, e0, e1, smem, full, empty, i, cur)) break;
+    // the work lists of CTA slots q = blockIdx.x, blockIdx.x + gridDim.x, ... (all of them when
+    // the launch has a CTA per work list)
+    for (int q = blockIdx.x; q < P.nct && ok; q += gridDim.x) {
+      const uint32_t e0 = __ldg(P.cta_e0 + q), e1 = __ldg(P.cta_e0 + q + 1);
+      ok = produce<FMT, PH, R>(J.j[m].L, e0, e1, smem, full, empty, i, cur);
+    }
+    if (!ok) break;
   }
   // the last copy issued into every slot has landed before the CTA exits
   if (lane == 0) {
@@ -612,6 +661,102 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
       } else {
         L.partial[size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk] = double(dot);
       }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// Phase 1, AFL codes, FP32 accumulation with two codes per window (code_pair): the lane's rc
+// values (rows sub, sub + G, ... of its X column), decoded as dec_f32 does, times the staged x
+// of their rows, summed in two FP32 partial sums (even and odd values). An odd last value comes
+// with the next (unused) code of its window; windows read at most two rows of 32 words past the
+// slice (inside the pad).
+template <bool WIDE>
+__device__ __forceinline__ float p1_pairs(int rc, uint32_t col_s, const ColDec &c, uint32_t xa, uint32_t xstep) {
+  float s0 = 0.f, s1 = 0.f;
+  uint32_t b = 0;
+  int r = 0;
+#pragma unroll 2
+  for (; r + 2 <= rc; r += 2, b += 2 * c.w, xa += 2 * xstep) {
+    uint32_t c0, c1;
+    code_pair<WIDE>(col_s, b, c.w, c0, c1);
+    s0 = fmaf(dec_f32(c0, c), ld_shared_f32(xa), s0);
+    s1 = fmaf(dec_f32(c1, c), ld_shared_f32(xa + xstep), s1);
+  }
+  if (r < rc) {
+    uint32_t c0, c1;
+    code_pair<WIDE>(col_s, b, c.w, c0, c1);
+    s0 = fmaf(dec_f32(c0, c), ld_shared_f32(xa), s0);
+  }
+  return s0 + s1;
+}
+
+__device__ bool consume_phase1_pairs(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                     uint64_t *empty) {
+  constexpr int FMT = FMT_AFL32;
+  constexpr size_t slot = slot_bytes<FMT, 0>();
+  const int t = threadIdx.x, lane = t & 31;
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const float *aux = reinterpret_cast<const float *>(sl + kPieceMax + kSlotPad);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    LaneHdr h{0xff, 0, 0, 0};
+    if (t < int(ph->ncols)) h = lane_hdrs(sl, ph)[t];
+    const bool active = h.seg != 0xff;
+    const ColDec c = col_dec(h.e & 0x7fu, h.m);
+    const bool narrow = __all_sync(kFull, !active || (c.fast32 && c.w <= 16));
+    float dot = 0.f;
+    uint32_t G = 1;
+    const Seg *sgp = nullptr;
+    bool lead = false;
+    if (active) {
+      const Seg &sg = segs[h.seg];
+      sgp = &sg;
+      G = 1u << sg.lg;
+      const int sub = t & int(G - 1);
+      lead = sub == 0;
+      const int rc = (int(sg.nr) - sub + int(G) - 1) >> sg.lg;  // rows sub, sub + G, ...
+      const uint32_t *col = Wd + bc_column(ph, t);
+      const uint32_t xa = smem_u32(aux + sg.xs + sub), xstep = 4u * G;
+      if (c.fast32) {
+        dot = narrow ? p1_pairs<false>(rc, smem_u32(col), c, xa, xstep) : p1_pairs<true>(rc, smem_u32(col), c, xa, xstep);
+      } else {
+        const float *xr = aux + sg.xs + sub;
+        uint32_t bit = 0;
+        if (c.mid32) {
+          // mantissas wider than FP32's: the FP64 route's values from FP32 operations
+          for (int r = 0; r < rc; ++r, bit += c.w) dot = fmaf(dec_mid32(bc_code32(col, bit), c), xr[r * int(G)], dot);
+        } else if (c.narrow) {
+          for (int r = 0; r < rc; ++r, bit += c.w)
+            dot = fmaf(float(dec_f64(bc_code32(col, bit), c)), xr[r * int(G)], dot);
+        } else {
+          for (int r = 0; r < rc; ++r, bit += c.w)
+            dot = fmaf(float(dec_f64(bc_code64(col, bit), c)), xr[r * int(G)], dot);
+        }
+      }
+    }
+    // the G lanes of a column (an aligned group) sum their row parts in a fixed order
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const float v = __shfl_xor_sync(kFull, dot, o);
+      if (o < G) dot += v;
+    }
+    if (lead) {
+      const Seg &sg = *sgp;
+      const float f = aux[sg.fs + h.j];
+      if (sg.x.nchunks == 1)
+        L.tw32[sg.tidx + h.j] = dot * f;
+      else
+        L.partial[size_t(sg.x.pbase) + size_t(h.j) * sg.x.nchunks + sg.x.chunk] = double(dot);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -792,6 +937,340 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
         y[gi] = yold + sum;  // the only update of this row (its leaf has one owner CTA)
       }
       parity ^= 1u;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  return true;
+}
+
+// Phase 2, AFL codes, FP32 accumulation with two codes per window: as consume_phase2_reg (the
+// same products dec_mul_f32 forms, the same row sums), but a warp whose lanes all have FP32-
+// pattern codes takes two rows per window (code_pair), and a leaf's row totals go to ysum in
+// cluster order (one store per row; k_scatter then adds them into y, so no register holds y or
+// the permutation during the leaf). The row after an odd row count decodes the next code of its
+// window (at most two rows of 32 words past the last warp region, inside the slot's pad) into a
+// row sum that is never stored.
+static_assert(8 * 128 <= kSlotPad + kAuxMax2 * 4, "phase-2 window reads stay inside the slot");
+
+template <bool WIDE>
+__device__ __forceinline__ void p2_pairs(float (&acc)[64], int nr, uint32_t col_s, const ColDec &c, float mult) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (8 * k >= nr) break;
+    const bool whole = 8 * k + 8 <= nr;  // the leaf's rows cover the chunk: no row checks
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = 4 * k + q;  // rows 2p, 2p + 1
+      if (!whole && 2 * p >= nr) break;
+      uint32_t c0, c1;
+      code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
+      acc[2 * p] += dec_mul_f32(c0, c, mult);
+      acc[2 * p + 1] += dec_mul_f32(c1, c, mult);
+    }
+  }
+}
+
+__device__ bool consume_phase2_pairs(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                     uint64_t *empty, double *red, uint32_t &parity) {
+  constexpr int FMT = FMT_AFL32;
+  constexpr size_t slot = slot_bytes<FMT, 1>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  float acc[64];
+#pragma unroll
+  for (int r = 0; r < 64; ++r) acc[r] = 0.f;
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const float *aux = reinterpret_cast<const float *>(sl + kPieceMax + kSlotPad);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+#pragma unroll
+      for (int r = 0; r < 64; ++r) acc[r] = 0.f;
+    }
+    float mult = 0.f;
+    uint32_t e = 0, m = 0;
+    const uint32_t *col = Wd;
+    bool active = false;
+    if (t < int(ph->ncols)) {
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
+        mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * float(sg.m_min) : aux[sg.xs + h.j];
+        e = h.e & 0x7fu;
+        m = h.m;
+        col = Wd + bc_column(ph, t);
+        active = true;
+      }
+    }
+    const ColDec c = col_dec(e, m);
+    if (__all_sync(kFull, !active || (c.fast32 && c.w <= 16))) {
+      if (active) p2_pairs<false>(acc, nr, smem_u32(col), c, mult);
+    } else if (__all_sync(kFull, !active || c.fast32)) {
+      if (active) p2_pairs<true>(acc, nr, smem_u32(col), c, mult);
+    } else {
+      // mantissas wider than FP32's: the FP64 route's values from FP32 operations
+      const bool mid = __all_sync(kFull, !active || c.mid32);
+      if (active) {
+        if (mid)
+          p2_rows<1, FMT>(acc, nr, col, c, mult);
+        else
+          p2_rows<2, FMT>(acc, nr, col, c, mult);
+      }
+    }
+    // the slot is not read after this point: hand it back before the leaf's reduction
+    const uint32_t row0 = ph->row0;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (flags & PF_END_LEAF) {
+      // reduce-scatter over the warp (as consume_phase2_reg): lane l ends with rows 2l, 2l + 1
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        const int half = 32 >> st;
+        const int mask = 16 >> st;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+          const float send = up ? acc[q] : acc[q + half];
+          const float keep = up ? acc[q + half] : acc[q];
+          acc[q] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+      }
+      const int rb = 2 * lane;
+      double *buf = red + parity * (kCWarps * 64);
+      buf[warp * 64 + rb] = double(acc[0]);
+      buf[warp * 64 + rb + 1] = double(acc[1]);
+      bar_consumers();
+      if (t < nr) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w4 = 0; w4 < kCWarps; ++w4) sum += buf[w4 * 64 + t];
+        L.ysum[row0 + uint32_t(t)] = sum;  // the row's total (its leaf has one owner CTA)
+      }
+      parity ^= 1u;
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
+// FP64 accumulation over AFL codes with one FP64 multiply-add per value. For a code of the FP32
+// fast path, v - 1 is exact in FP32 (at most 24 significant bits, 0 or >= 1), so its FP64
+// pattern follows from the FP32 one by integer operations (rebias the exponent by
+// 1023 - 127, widen the mantissa); the value is then fma(v - 1, +-mult, acc) in FP64 with the
+// code's sign on the multiplier. Other codes take the FP64 route: v - 1.0 in FP64, then the
+// multiply-add.
+// ---------------------------------------------------------------------------------------------
+// FP64 value of a nonnegative FP32 bit pattern P of a normal number or zero
+__device__ __forceinline__ double f32pat_to_f64(uint32_t P) {
+  const uint32_t hi = P != 0u ? (P >> 3) + 0x38000000u : 0u;
+  return __hiloint2double(int(hi), int(P << 29));
+}
+// v - 1 of a code (fast path, code at bit 0, other bits above) as FP64
+__device__ __forceinline__ double vm1_f64(uint32_t code, const ColDec &c) {
+  const float v = __uint_as_float((code & c.em_mask) * c.scale + 0x3F800000u) - 1.0f;
+  return f32pat_to_f64(__float_as_uint(v));
+}
+// +-s with the code's sign
+__device__ __forceinline__ double signed_f64(uint32_t code, const ColDec &c, double s) {
+  return __hiloint2double(__double2hiint(s) ^ int((code << c.sshift) & 0x80000000u), __double2loint(s));
+}
+
+// Phase 2, FP64 accumulation, AFL codes: one lane per column slice of the leaf, FP64 row sums
+// in registers (one multiply-add per value), a butterfly over the warp and the four warps'
+// sums into ysum at the end of the leaf (as consume_phase2_pairs).
+template <bool WIDE>
+__device__ __forceinline__ void p2_pairs64(double (&acc)[64], int nr, uint32_t col_s, const ColDec &c, double mult) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    if (8 * k >= nr) break;
+    const bool whole = 8 * k + 8 <= nr;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = 4 * k + q;
+      if (!whole && 2 * p >= nr) break;
+      uint32_t c0, c1;
+      code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
+      acc[2 * p] = fma(vm1_f64(c0, c), signed_f64(c0, c, mult), acc[2 * p]);
+      acc[2 * p + 1] = fma(vm1_f64(c1, c), signed_f64(c1, c, mult), acc[2 * p + 1]);
+    }
+  }
+}
+// the FP64 route for codes outside the fast path (rows past the leaf decode the slice's first
+// value and are dropped)
+__device__ __forceinline__ void p2_rows64(double (&acc)[64], int nr, const uint32_t *col, const ColDec &c, double mult) {
+#pragma unroll
+  for (int r = 0; r < 64; ++r) {
+    if (r >= nr) break;
+    acc[r] = fma(dec_f64(bc_code64(col, uint32_t(r) * c.w), c), mult, acc[r]);
+  }
+}
+
+__device__ bool consume_phase2_f64(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                   uint64_t *empty, double *red, uint32_t &parity) {
+  constexpr int FMT = FMT_AFL64;
+  constexpr size_t slot = slot_bytes<FMT, 1>();
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  double acc[64];
+#pragma unroll
+  for (int r = 0; r < 64; ++r) acc[r] = 0.0;
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const double *aux = reinterpret_cast<const double *>(sl + kPieceMax + kSlotPad);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const int nr = ph->nr;
+    const uint32_t flags = ph->flags;
+    if (flags & PF_START_LEAF) {
+#pragma unroll
+      for (int r = 0; r < 64; ++r) acc[r] = 0.0;
+    }
+    double mult = 0.0;
+    uint32_t e = 0, m = 0;
+    const uint32_t *col = Wd;
+    bool active = false;
+    if (t < int(ph->ncols)) {
+      const LaneHdr h = lane_hdrs(sl, ph)[t];
+      if (h.seg != 0xff) {
+        const Seg &sg = segs[h.seg];
+        mult = sg.kind == SEG_DENSE ? aux[sg.xs + h.j] * sg.m_min : aux[sg.xs + h.j];
+        e = h.e & 0x7fu;
+        m = h.m;
+        col = Wd + bc_column(ph, t);
+        active = true;
+      }
+    }
+    const ColDec c = col_dec(e, m);
+    if (__all_sync(kFull, !active || (c.fast32 && c.w <= 16))) {
+      if (active) p2_pairs64<false>(acc, nr, smem_u32(col), c, mult);
+    } else if (__all_sync(kFull, !active || c.fast32)) {
+      if (active) p2_pairs64<true>(acc, nr, smem_u32(col), c, mult);
+    } else if (active) {
+      p2_rows64(acc, nr, col, c, mult);
+    }
+    // the slot is not read after this point: hand it back before the leaf's reduction
+    const uint32_t row0 = ph->row0;
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (flags & PF_END_LEAF) {
+#pragma unroll
+      for (int st = 0; st < 5; ++st) {
+        const int half = 32 >> st;
+        const int mask = 16 >> st;
+        const bool up = (lane & mask) != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+          const double send = up ? acc[q] : acc[q + half];
+          const double keep = up ? acc[q + half] : acc[q];
+          acc[q] = keep + __shfl_xor_sync(kFull, send, mask);
+        }
+      }
+      const int rb = 2 * lane;
+      double *buf = red + parity * (kCWarps * 64);
+      buf[warp * 64 + rb] = acc[0];
+      buf[warp * 64 + rb + 1] = acc[1];
+      bar_consumers();
+      if (t < nr) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w4 = 0; w4 < kCWarps; ++w4) sum += buf[w4 * 64 + t];
+        L.ysum[row0 + uint32_t(t)] = sum;  // the row's total (its leaf has one owner CTA)
+      }
+      parity ^= 1u;
+    }
+  }
+  return true;
+}
+
+// Phase 1, FP64 accumulation, AFL codes: the lane's values times the staged FP64 x of their rows,
+// one multiply-add per value into two FP64 partial sums.
+template <bool WIDE>
+__device__ __forceinline__ double p1_pairs64(int rc, uint32_t col_s, const ColDec &c, const double *xr, int xs) {
+  double s0 = 0.0, s1 = 0.0;
+  uint32_t b = 0;
+  int r = 0;
+#pragma unroll 2
+  for (; r + 2 <= rc; r += 2, b += 2 * c.w) {
+    uint32_t c0, c1;
+    code_pair<WIDE>(col_s, b, c.w, c0, c1);
+    s0 = fma(vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
+    s1 = fma(vm1_f64(c1, c), signed_f64(c1, c, xr[(r + 1) * xs]), s1);
+  }
+  if (r < rc) {
+    uint32_t c0, c1;
+    code_pair<WIDE>(col_s, b, c.w, c0, c1);
+    s0 = fma(vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
+  }
+  return s0 + s1;
+}
+
+__device__ bool consume_phase1_f64(const DevLayout &L, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                   uint64_t *empty) {
+  constexpr int FMT = FMT_AFL64;
+  constexpr size_t slot = slot_bytes<FMT, 0>();
+  const int t = threadIdx.x, lane = t & 31;
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const double *aux = reinterpret_cast<const double *>(sl + kPieceMax + kSlotPad);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    LaneHdr h{0xff, 0, 0, 0};
+    if (t < int(ph->ncols)) h = lane_hdrs(sl, ph)[t];
+    const bool active = h.seg != 0xff;
+    const ColDec c = col_dec(h.e & 0x7fu, h.m);
+    const bool narrow = __all_sync(kFull, !active || (c.fast32 && c.w <= 16));
+    double dot = 0.0;
+    uint32_t G = 1;
+    const Seg *sgp = nullptr;
+    bool lead = false;
+    if (active) {
+      const Seg &sg = segs[h.seg];
+      sgp = &sg;
+      G = 1u << sg.lg;
+      const int sub = t & int(G - 1);
+      lead = sub == 0;
+      const int rc = (int(sg.nr) - sub + int(G) - 1) >> sg.lg;  // rows sub, sub + G, ...
+      const uint32_t *col = Wd + bc_column(ph, t);
+      const double *xr = aux + sg.xs + sub;
+      if (c.fast32) {
+        dot = narrow ? p1_pairs64<false>(rc, smem_u32(col), c, xr, int(G)) : p1_pairs64<true>(rc, smem_u32(col), c, xr, int(G));
+      } else {
+        uint32_t bit = 0;
+        for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(bc_code64(col, bit), c), xr[r * int(G)], dot);
+      }
+    }
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const double v = __shfl_xor_sync(kFull, dot, o);
+      if (o < G) dot += v;
+    }
+    if (lead) {
+      const Seg &sg = *sgp;
+      const double f = aux[sg.fs + h.j];
+      if (sg.x.nchunks == 1)
+        L.tw64[sg.tidx + h.j] = dot * f;
+      else
+        L.partial[size_t(sg.x.pbase) + size_t(h.j) * sg.x.nchunks + sg.x.chunk] = dot;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -1243,8 +1722,13 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
 // Persistent product kernel over the products of one launch (J.n <= NB). Every CTA walks its
 // range of each product's piece stream in turn; the ring slots and their mbarrier phases run on
 // across products.
+// resident CTAs per SM the product kernels are compiled for: the FP64-accumulation kernels keep
+// 64 FP64 row sums per thread in phase 2
+template <int FMT>
+constexpr int kMinBlocks = FMT == FMT_AFL64 ? 2 : 4;
+
 template <int FMT, int PH, int R, int NB>
-__global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__ Jobs<NB> J) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks<FMT>) k_product(const __grid_constant__ Jobs<NB> J) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr size_t slot = slot_bytes<FMT, PH, R>();
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
@@ -1253,7 +1737,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__
   using A = typename Tr<FMT>::A;
   A *tiles = reinterpret_cast<A *>(red + 2 * kCWarps * 64);
   uint32_t np_all = 0;
-  for (int m = 0; m < J.n; ++m) np_all += __ldg(J.j[m].L.ph[PH].cta_np + blockIdx.x);
+  for (int m = 0; m < J.n; ++m)
+    for (int q = blockIdx.x; q < J.j[m].L.ph[PH].nct; q += gridDim.x) np_all += __ldg(J.j[m].L.ph[PH].cta_np + q);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
@@ -1268,21 +1753,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_product(const __grid_constant__
     return;
   }
   uint32_t it = 0, parity = 0;
-  for (int m = 0; m < J.n; ++m) {
+  for (int m = 0; m < J.n; ++m)
+  for (int q = blockIdx.x; q < J.j[m].L.ph[PH].nct; q += gridDim.x) {
     const Job &jb = J.j[m];
-    const uint32_t np = __ldg(jb.L.ph[PH].cta_np + blockIdx.x);
+    const uint32_t np = __ldg(jb.L.ph[PH].cta_np + q);
     bool ok;
     if constexpr (R > 1) {
       if constexpr (PH == 0)
         ok = consume_phase1_multi(jb, np, it, smem, full, empty);
       else
         ok = consume_phase2_multi_mma(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
+    } else if constexpr (PH == 0 && FMT == FMT_AFL32) {
+      ok = consume_phase1_pairs(jb.L, np, it, smem, full, empty);
+    } else if constexpr (PH == 0 && FMT == FMT_AFL64) {
+      ok = jb.L.vfmt == VF_AFL ? consume_phase1_f64(jb.L, np, it, smem, full, empty)
+                               : consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
     } else if constexpr (PH == 0) {
       ok = consume_phase1<FMT>(jb.L, np, it, smem, full, empty);
+    } else if constexpr (FMT == FMT_AFL32) {
+      ok = consume_phase2_pairs(jb.L, np, it, smem, full, empty, red, parity);
     } else if constexpr (kFP32<FMT>) {
       ok = consume_phase2_reg<FMT>(jb.L, np, it, smem, full, empty, red, jb.y, parity);
     } else if constexpr (FMT == FMT_AFL64) {
-      ok = consume_phase2<FMT>(jb.L, np, it, smem, full, empty, red, tiles, jb.y, parity);
+      ok = jb.L.vfmt == VF_AFL ? consume_phase2_f64(jb.L, np, it, smem, full, empty, red, parity)
+                               : consume_phase2<FMT>(jb.L, np, it, smem, full, empty, red, tiles, jb.y, parity);
     } else {
       ok = consume_phase2_rows<FMT>(jb.L, np, it, smem, full, empty, red, jb.y, parity);
     }
@@ -1378,7 +1872,8 @@ namespace {
 
 struct DevProps {
   int sms = 0;
-  int occ[2] = {0, 0};  // resident CTAs per SM of the phase-1 / phase-2 kernels (FP32 path)
+  int occ[2] = {0, 0};    // resident CTAs per SM of the phase-1 / phase-2 kernels (FP32 path)
+  int occ64[2] = {0, 0};  // the same for the FP64-accumulation kernels
 };
 std::mutex g_props_mu;
 DevProps g_props[64];
@@ -1423,6 +1918,12 @@ const DevProps &props(int dev) {
                                                   smem_bytes<FMT_AFL32, 1>());
     P.occ[0] = o0 < 1 ? 1 : o0;
     P.occ[1] = o1 < 1 ? 1 : o1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL64, 0, 1, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL64, 0>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL64, 1, 1, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL64, 1>());
+    P.occ64[0] = o0 < 1 ? 1 : o0;
+    P.occ64[1] = o1 < 1 ? 1 : o1;
     if (cur != dev) cudaSetDevice(cur);
   }
   return P;
@@ -1434,10 +1935,11 @@ int cuda_status(const char *what) {
   return HLR_OK;
 }
 
-// Launch the four kernels of the products in J (all of one device, so all share the persistent
-// grid sizes): permute, phase 1, combine of split blocks, phase 2. ev (optional): 4 events.
+// Launch the kernels of the products in J (all of one device, so all share the persistent grid
+// sizes): permute, phase 1, combine of split blocks, phase 2 and, for the single-RHS AFL FP32
+// product, the scatter of the row totals into y. ev (optional): kProfileEv events.
 template <int FMT, int R, int NB>
-void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev) {
+void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev, int share = 0) {
   if (J.n <= 0) return;
   int64_t nmax = 0, ncnt = 0;
   uint32_t np0 = 0, np1 = 0;
@@ -1448,7 +1950,19 @@ void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev) {
     np0 += uint32_t(L.ph[0].np);
     np1 += uint32_t(L.ph[1].np);
   }
-  const int nct0 = J.j[0].L.ph[0].nct, nct1 = J.j[0].L.ph[1].nct;
+  // share (1..7): about share/8 of the CTA slots of the persistent kernels, each CTA walking the
+  // work lists of several slots, so that concurrent work keeps the rest of every SM
+  auto cap = [share](int nct) { return share > 0 && share < 8 ? std::max(1, (nct * share + 7) / 8) : nct; };
+  int nct0 = cap(J.j[0].L.ph[0].nct), nct1 = cap(J.j[0].L.ph[1].nct);
+  if constexpr (FMT == FMT_AFL64) {
+    // fewer of these are resident than there are work lists (made for the FP32 kernels): one
+    // wave of CTAs, each walking several work lists
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const DevProps &P = props(dev);
+    nct0 = std::min(nct0, P.sms * P.occ64[0]);
+    nct1 = std::min(nct1, P.sms * P.occ64[1]);
+  }
   const dim3 gp(unsigned(std::min<int64_t>((nmax + 255) / 256, 4096)), unsigned(J.n));
   if (ev) cudaEventRecord(ev[0], st);
   if constexpr (R == 1)
@@ -1464,13 +1978,16 @@ void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[2], st);
   if (np1 > 0) k_product<FMT, 1, R, NB><<<nct1, kThreads, smem_bytes<FMT, 1, R>(), st>>>(J);
   if (ev) cudaEventRecord(ev[3], st);
+  if constexpr ((FMT == FMT_AFL32 || FMT == FMT_AFL64) && R == 1)
+    if (np1 > 0) k_scatter<NB><<<gp, 256, 0, st>>>(J);
+  if (ev) cudaEventRecord(ev[4], st);
 }
 
 // Events of the next profiled product (nullptr if not profiling or the ring is full).
 cudaEvent_t *profile_slot(Handle &H, int flags) {
   if (!(flags & HLR_PROFILE)) return nullptr;
   if (H.prof_ev.empty()) {
-    H.prof_ev.resize(4 * size_t(kProfileCap), nullptr);
+    H.prof_ev.resize(kProfileEv * size_t(kProfileCap), nullptr);
     for (auto &e : H.prof_ev) {
       cudaEvent_t ev;
       cudaEventCreate(&ev);
@@ -1478,7 +1995,7 @@ cudaEvent_t *profile_slot(Handle &H, int flags) {
     }
   }
   if (H.prof_n >= kProfileCap) return nullptr;
-  return reinterpret_cast<cudaEvent_t *>(&H.prof_ev[4 * size_t(H.prof_n++)]);
+  return reinterpret_cast<cudaEvent_t *>(&H.prof_ev[kProfileEv * size_t(H.prof_n++)]);
 }
 
 Job single_job(const Handle &H, const double *x, double *y) {
@@ -1506,21 +2023,22 @@ int launch_matvec(Handle &H, const double *x, double *y, int flags, void *stream
   props(H.device);
   cudaEvent_t *ev = profile_slot(H, flags);
   const int acc = flags & 0xff;
+  const int share = (flags >> 16) & 15;
   Jobs<1> J{};
   J.n = 1;
   J.j[0] = single_job(H, x, y);
   if (H.L.raw)
-    launch_jobs<FMT_RAW64, 1, 1>(J, st, ev);
+    launch_jobs<FMT_RAW64, 1, 1>(J, st, ev, share);
   else if (acc != HLR_ACC_FP32)
-    launch_jobs<FMT_AFL64, 1, 1>(J, st, ev);  // FP64 decode of every value format
+    launch_jobs<FMT_AFL64, 1, 1>(J, st, ev, share);  // FP64 decode of every value format
   else if (H.L.vfmt == VF_BFL)
-    launch_jobs<FMT_BFL32, 1, 1>(J, st, ev);
+    launch_jobs<FMT_BFL32, 1, 1>(J, st, ev, share);
   else if (H.L.vfmt == VF_DFL)
-    launch_jobs<FMT_DFL32, 1, 1>(J, st, ev);
+    launch_jobs<FMT_DFL32, 1, 1>(J, st, ev, share);
   else if (H.L.vfmt == VF_MP)
-    launch_jobs<FMT_MP32, 1, 1>(J, st, ev);
+    launch_jobs<FMT_MP32, 1, 1>(J, st, ev, share);
   else
-    launch_jobs<FMT_AFL32, 1, 1>(J, st, ev);
+    launch_jobs<FMT_AFL32, 1, 1>(J, st, ev, share);
   return cuda_status("hlr_matvec: launch");
 }
 
@@ -1562,10 +2080,10 @@ struct Batcher {
   Jobs<kMaxBatch> J{};
   std::vector<std::pair<const Handle *, int>> keys;
   cudaStream_t st;
-  int device = -1;
-  explicit Batcher(cudaStream_t s) : st(s) { J.n = 0; }
+  int share;
+  explicit Batcher(cudaStream_t s, int sh) : st(s), share(sh) { J.n = 0; }
   void flush() {
-    if (J.n > 0) launch_jobs<FMT, R, kMaxBatch>(J, st, nullptr);
+    if (J.n > 0) launch_jobs<FMT, R, kMaxBatch>(J, st, nullptr, share);
     J.n = 0;
     keys.clear();
   }
@@ -1591,13 +2109,14 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   props(dev);
   const bool fp32 = (flags & 0xff) == HLR_ACC_FP32;
   const int multi_from = (flags & HLR_MULTI) ? 1 : 2;  // fewest columns that take the multi-RHS kernels
-  Batcher<FMT_AFL32, 1> b32(st);
-  Batcher<FMT_BFL32, 1> bbfl(st);
-  Batcher<FMT_DFL32, 1> bdfl(st);
-  Batcher<FMT_MP32, 1> bmp(st);
-  Batcher<FMT_AFL64, 1> b64(st);
-  Batcher<FMT_RAW64, 1> braw(st);
-  Batcher<FMT_AFL32, kRB> bm(st);  // multi-column passes decode the AFL family only
+  const int share = (flags >> 16) & 15;
+  Batcher<FMT_AFL32, 1> b32(st, share);
+  Batcher<FMT_BFL32, 1> bbfl(st, share);
+  Batcher<FMT_DFL32, 1> bdfl(st, share);
+  Batcher<FMT_MP32, 1> bmp(st, share);
+  Batcher<FMT_AFL64, 1> b64(st, share);
+  Batcher<FMT_RAW64, 1> braw(st, share);
+  Batcher<FMT_AFL32, kRB> bm(st, share);  // multi-column passes decode the AFL family only
   // pass scratch first (growing it frees the old one, which no pending product may still use)
   for (int q = 0; q < nreq; ++q) {
     if (nrhs[q] < multi_from || !fp32 || H[q]->L.raw || H[q]->L.vfmt != VF_AFL) continue;
@@ -1658,11 +2177,11 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
 }
 
 int profile_read(Handle &H, double *ms, int *calls) {
-  ms[0] = ms[1] = ms[2] = 0.0;
+  for (int k = 0; k < kProfileEv - 1; ++k) ms[k] = 0.0;
   for (int i = 0; i < H.prof_n; ++i) {
-    cudaEvent_t *ev = reinterpret_cast<cudaEvent_t *>(&H.prof_ev[4 * size_t(i)]);
-    if (cudaEventSynchronize(ev[3]) != cudaSuccess) return cuda_status("hlr_profile_read");
-    for (int k = 0; k < 3; ++k) {
+    cudaEvent_t *ev = reinterpret_cast<cudaEvent_t *>(&H.prof_ev[kProfileEv * size_t(i)]);
+    if (cudaEventSynchronize(ev[kProfileEv - 1]) != cudaSuccess) return cuda_status("hlr_profile_read");
+    for (int k = 0; k < kProfileEv - 1; ++k) {
       float t = 0.f;
       cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
       ms[k] += t;
@@ -1786,6 +2305,25 @@ int launch_decode_units_static(const Handle &H, double *out, void *stream) {
                                        reinterpret_cast<const double *>(base + o_mmin), base + o_e, base + o_m, ns,
                                        H.L.raw, H.L.vfmt, out);
   return cuda_status("hlr_decode_units_static");
+}
+
+// Failure-detection self-test: thread 0 initialises an mbarrier on which nothing ever arrives
+// and waits for its first phase with the product kernels' bounded wait, limited to `cycles`;
+// when the wait gives up it records the failure in the status word as a product kernel does.
+__global__ void k_wait_expire(uint32_t *status, long long cycles) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait(&bar, 0, cycles)) atomicOr(status, 1u);
+  }
+}
+
+int launch_wait_expire(const Handle &H, long long cycles, void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  k_wait_expire<<<1, 32, 0, st>>>(H.L.status, cycles);
+  return cuda_status("hlr_selftest_wait");
 }
 
 int launch_decode_stream(const uint8_t *stream, int64_t n, double m_min, int e, int m, double *out, void *stream_) {

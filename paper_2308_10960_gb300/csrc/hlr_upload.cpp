@@ -30,6 +30,14 @@
 
 namespace hlr {
 
+// Precision of a unit (Section 3.3). A dense leaf is one unit at the accuracy eps of Eq. 1 (the
+// MP comparison format keeps dense leaves in FP64, i.e. any precision below 2^-53). Column i of
+// a lowrank leaf W diag(sigma) X^T (W and X columns alike) gets the adaptive precision
+// u_i = delta / sigma_i with delta = eps sigma_0, the truncation threshold of Eq. 1 in the
+// spectral norm: the larger sigma_i, the more mantissa bits its columns keep.
+double dense_precision(int format, double eps) { return format == HLR_FMT_MP ? 0x1p-60 : eps; }
+double column_precision(double eps, double sigma0, double sigma_i) { return (eps * sigma0) / sigma_i; }
+
 static thread_local std::string g_err;
 static std::mutex g_mu;
 static std::unordered_map<uint64_t, std::unique_ptr<Handle>> g_handles;
@@ -76,10 +84,12 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL && d->format != HLR_FMT_MP)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
   int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
-  if (d->tuning != 0) {
-    const int sl = d->tuning & 15, ll = (d->tuning >> 4) & 15, kb = (d->tuning >> 8) & 255;
-    if (d->format == HLR_FMT_FP64 || sl < 5 || sl > 7 || ll < 5 || ll > 6 || kb < 4 || kb > kPieceMax / 1024 ||
-        (d->tuning >> 16) != 0)
+  if ((d->tuning >> 16) & ~1) return set_error(HLR_ERR_INVALID, "hlr_upload: unknown tuning flags");
+  const bool keep_map = (d->tuning & HLR_DECODE_MAP) != 0;
+  const int32_t layout = d->tuning & 0xffff;
+  if (layout != 0) {
+    const int sl = layout & 15, ll = (layout >> 4) & 15, kb = (layout >> 8) & 255;
+    if (d->format == HLR_FMT_FP64 || sl < 5 || sl > 7 || ll < 5 || ll > 6 || kb < 4 || kb > kPieceMax / 1024)
       return set_error(HLR_ERR_INVALID, "hlr_upload: bad tuning (see HLR_TUNING; AFL format only)");
     sub_rows = 1 << sl;
     leaf_rows = 1 << ll;
@@ -181,21 +191,20 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       in.blk_unit0[b] = int64_t(usrc.size());
       usrc.push_back(B.D);
       in.unit_len.push_back(B.nrows * B.ncols);
-      uprec.push_back(d->format == HLR_FMT_MP ? 0.0 : d->eps);  // MP keeps dense leaves in FP64
+      uprec.push_back(dense_precision(d->format, d->eps));
       rowside.push_back(1);
     } else if (B.rank > 0) {
       in.blk_unit0[b] = int64_t(usrc.size());
-      const double delta = d->eps * B.sigma[0];
       for (int i = 0; i < B.rank; ++i) {
         usrc.push_back(B.W + i * B.nrows);
         in.unit_len.push_back(B.nrows);
-        uprec.push_back(delta / B.sigma[i]);
+        uprec.push_back(column_precision(d->eps, B.sigma[0], B.sigma[i]));
         rowside.push_back(1);
       }
       for (int i = 0; i < B.rank; ++i) {
         usrc.push_back(B.X + i * B.ncols);
         in.unit_len.push_back(B.ncols);
-        uprec.push_back(delta / B.sigma[i]);
+        uprec.push_back(column_precision(d->eps, B.sigma[0], B.sigma[i]));
         rowside.push_back(0);
       }
     }
@@ -217,7 +226,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   // A phase-2 lane holds one column over the task's rows, in a warp region of 32 such lanes:
   // 64 rows of 64-bit codes (FP64 values of MP, DFL at m' = 52) make a 16 KiB region, more than
   // a piece holds with its headers, so the default layout then takes tasks of 32 rows.
-  if (afl && d->tuning == 0) {
+  if (afl && layout == 0) {
     for (int64_t u = 0; u < nunits; ++u)
       if (rowside[u] && 64 + 128 * ((int64_t(in.prm[u].w) * kLeafRows + 31) / 32) > int64_t(piece_max)) {
         leaf_rows = kLeafRows / 2;
@@ -257,7 +266,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   int nct[2] = {0, 0};
   if (ctas_per_phase(dev, nct) <= 0) return set_error(HLR_ERR_CUDA, "hlr_upload: cannot query the device");
   PackOutput po;
-  const bool want_map = values <= kDecodeMapMaxValues;
+  const bool want_map = keep_map || values <= kDecodeMapMaxValues;
   int rc = pack_work(in, nct, want_map, &po);
   if (rc) return rc;
 
@@ -324,6 +333,8 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   off = align_up(off + 4 * (size_t(rank_sum) + 8), 256);
   const size_t o_part = off;
   off = align_up(off + 8 * size_t(po.part_total) + 8, 256);
+  const size_t o_ysum = off;
+  off = align_up(off + 8 * (size_t(n) + 8), 256);
   const size_t o_status = off;
   off = align_up(off + 64, 256);
   const size_t o_xdev = off;
@@ -393,6 +404,7 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   L.tw64 = reinterpret_cast<double *>(A + o_tw64);
   L.tw32 = reinterpret_cast<float *>(A + o_tw32);
   L.partial = reinterpret_cast<double *>(A + o_part);
+  L.ysum = reinterpret_cast<double *>(A + o_ysum);
   L.comb = reinterpret_cast<const Combine *>(A + o_comb);
   L.status = reinterpret_cast<uint32_t *>(A + o_status);
   L.xdev = reinterpret_cast<double *>(A + o_xdev);
@@ -459,7 +471,10 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   I.flops = fl;
   const uint64_t hb = afl ? 16 : 0;
   I.phase1_bytes = xs + hb * nx + 16 * uint64_t(rank_sum) + 4 * uint64_t(n);
-  I.launches = 1 + (po.ph[0].piece_off.size() > 1) + (po.ncnt > 0) + (po.ph[1].piece_off.size() > 1);
+  // the FP32-accumulation product of the AFL and AFLP formats adds its phase-2 row sums into y
+  // in one more kernel
+  I.launches = 1 + (po.ph[0].piece_off.size() > 1) + (po.ncnt > 0) + (po.ph[1].piece_off.size() > 1) +
+               ((afl && L.vfmt == VF_AFL && po.ph[1].piece_off.size() > 1) ? 1 : 0);
   I.phase2_bytes = (stream_bytes - xs) + hb * (uint64_t(nunits) - nx) + 8 * uint64_t(rank_sum) + 32 * uint64_t(n);
 
   std::lock_guard<std::mutex> lk(g_mu);
@@ -500,8 +515,9 @@ extern "C" int hlr_matvec(hlr_handle h, const double *x, double *y, int flags, v
   Handle *H = lookup(h);
   if (!H) return set_error(HLR_ERR_INVALID, "hlr_matvec: unknown handle");
   if (!x || !y) return set_error(HLR_ERR_INVALID, "hlr_matvec: null vector");
-  const int acc = flags & ~HLR_PROFILE;
-  if (acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_matvec: bad flags");
+  const int acc = flags & ~(HLR_PROFILE | HLR_SM_SHARE(15));
+  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags >> 16) & 15) > 8)
+    return set_error(HLR_ERR_INVALID, "hlr_matvec: bad flags");
   const int64_t n = H->L.n;
   const char *xb = reinterpret_cast<const char *>(x);
   const char *yb = reinterpret_cast<const char *>(y);
@@ -524,6 +540,14 @@ extern "C" int hlr_check(hlr_handle h, void *stream) {
                                           std::to_string(s[0]) + ")");
   }
   return HLR_OK;
+}
+
+extern "C" int hlr_selftest_wait(hlr_handle h, int64_t cycles, void *stream) {
+  Handle *H = lookup(h);
+  if (!H) return set_error(HLR_ERR_INVALID, "hlr_selftest_wait: unknown handle");
+  if (cycles < 1000 || cycles > (int64_t(1) << 31))
+    return set_error(HLR_ERR_INVALID, "hlr_selftest_wait: cycles must be in [1000, 2^31]");
+  return launch_wait_expire(*H, static_cast<long long>(cycles), stream);
 }
 
 extern "C" int hlr_decode_units(hlr_handle h, double *out, int64_t cap, void *stream) {
@@ -554,8 +578,9 @@ extern "C" int hlr_matvec_host(hlr_handle h, const double *x, double *y, int fla
   Handle *H = lookup(h);
   if (!H) return set_error(HLR_ERR_INVALID, "hlr_matvec_host: unknown handle");
   if (!x || !y) return set_error(HLR_ERR_INVALID, "hlr_matvec_host: null vector");
-  const int acc = flags & ~HLR_PROFILE;
-  if (acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) return set_error(HLR_ERR_INVALID, "hlr_matvec_host: bad flags");
+  const int acc = flags & ~(HLR_PROFILE | HLR_SM_SHARE(15));
+  if ((acc != HLR_ACC_FP64 && acc != HLR_ACC_FP32) || ((flags >> 16) & 15) > 8)
+    return set_error(HLR_ERR_INVALID, "hlr_matvec_host: bad flags");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = 8 * size_t(H->L.n);
   cudaError_t ce = cudaMemcpyAsync(H->L.xdev, x, bytes, cudaMemcpyHostToDevice, st);
@@ -566,5 +591,59 @@ extern "C" int hlr_matvec_host(hlr_handle h, const double *x, double *y, int fla
   ce = cudaMemcpyAsync(y, H->L.ydev, bytes, cudaMemcpyDeviceToHost, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string("hlr_matvec_host: ") + cudaGetErrorString(ce));
+  return HLR_OK;
+}
+
+extern "C" int hlr_unit_list(const hlr_hmatrix_desc *d, int64_t *off, double *prec, double *values, int64_t cap_units,
+                             int64_t cap_values, int64_t *nunits, int64_t *nvalues) {
+  using namespace hlr;
+  if (!d || (d->nblocks > 0 && !d->blocks) || d->nblocks < 0 || !nunits || !nvalues)
+    return set_error(HLR_ERR_INVALID, "hlr_unit_list: bad arguments");
+  const bool afl = d->format != HLR_FMT_FP64;
+  if (afl && !(d->eps > 0.0 && d->eps < 1.0)) return set_error(HLR_ERR_INVALID, "hlr_unit_list: eps must be in (0, 1)");
+  int64_t nu = 0, nv = 0;
+  for (int64_t b = 0; b < d->nblocks; ++b) {
+    const hlr_block_desc &B = d->blocks[b];
+    if (B.nrows < 0 || B.ncols < 0) return set_error(HLR_ERR_INVALID, "hlr_unit_list: negative block size");
+    if (B.kind == HLR_DENSE) {
+      if (!B.D && B.nrows * B.ncols > 0) return set_error(HLR_ERR_INVALID, "hlr_unit_list: dense block without data");
+      nu += 1;
+      nv += B.nrows * B.ncols;
+    } else if (B.kind == HLR_LOWRANK) {
+      if (B.rank < 0 || B.rank > std::min(B.nrows, B.ncols))
+        return set_error(HLR_ERR_INVALID, "hlr_unit_list: bad rank in block " + std::to_string(b));
+      if (B.rank > 0 && (!B.W || !B.X || !B.sigma))
+        return set_error(HLR_ERR_INVALID, "hlr_unit_list: lowrank block without factors");
+      for (int i = 0; i < B.rank; ++i)
+        if (!(B.sigma[i] > 0.0) || !std::isfinite(B.sigma[i]) || B.sigma[i] > B.sigma[0])
+          return set_error(HLR_ERR_INVALID, "hlr_unit_list: sigma must be positive, finite and led by its maximum");
+      nu += 2 * int64_t(B.rank);
+      nv += int64_t(B.rank) * (B.nrows + B.ncols);
+    } else {
+      return set_error(HLR_ERR_INVALID, "hlr_unit_list: unknown block kind");
+    }
+  }
+  *nunits = nu;
+  *nvalues = nv;
+  if ((off && cap_units < nu + 1) || (prec && cap_units < nu) || (values && cap_values < nv))
+    return set_error(HLR_ERR_OOM, "hlr_unit_list: output arrays too small");
+  int64_t u = 0, v = 0;
+  auto put = [&](const double *src, int64_t len, double p) {
+    if (off) off[u] = v;
+    if (prec) prec[u] = p;
+    if (values && len > 0) std::memcpy(values + v, src, size_t(len) * 8);
+    ++u;
+    v += len;
+  };
+  for (int64_t b = 0; b < d->nblocks; ++b) {
+    const hlr_block_desc &B = d->blocks[b];
+    if (B.kind == HLR_DENSE) {
+      put(B.D, B.nrows * B.ncols, dense_precision(d->format, d->eps));
+    } else {
+      for (int i = 0; i < B.rank; ++i) put(B.W + i * B.nrows, B.nrows, column_precision(d->eps, B.sigma[0], B.sigma[i]));
+      for (int i = 0; i < B.rank; ++i) put(B.X + i * B.ncols, B.ncols, column_precision(d->eps, B.sigma[0], B.sigma[i]));
+    }
+  }
+  if (off) off[u] = v;
   return HLR_OK;
 }

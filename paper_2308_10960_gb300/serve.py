@@ -10,7 +10,10 @@ solves against several matrices kept resident on one GPU.
   result does not depend on what it is batched with, so a request gets the same bits alone and
   in the mix.
 * Solves: unpreconditioned CG (``hlr_solve_cg``) runs in worker threads on their own streams,
-  overlapping the product batches; the library call releases the interpreter lock.
+  overlapping the product batches; the library call releases the interpreter lock. Its
+  product kernels take a share of the CTA slots (``HLR_SM_SHARE``, half by default) and it
+  reads its residual from the host only every few iterations, so product batches find room on
+  the SMs while solves run.
 * A matrix runs at most one product batch and at most one solve at a time: the batches use the
   multi-RHS pass scratch of its handle, the solves the single-RHS scratch and the CG workspace,
   so one of each may overlap.
@@ -243,7 +246,7 @@ class GpuBackend:
     """Drives the library. `host_mats` maps names to objects with ``upload(fmt, stream=...)``
     returning a DeviceHMatrix (HostHMatrix, or any adapter); they are uploaded on admission."""
 
-    def __init__(self, host_mats: dict, acc_cg: str = "fp32"):
+    def __init__(self, host_mats: dict, acc_cg: str = "fp32", solve_share: int = 4):
         import torch
         from . import matvec_batched
         self.torch = torch
@@ -251,6 +254,9 @@ class GpuBackend:
         self.host = dict(host_mats)
         self.dev = {}
         self.acc_cg = acc_cg
+        # solves run their product kernels on solve_share eighths of the CTA slots
+        # (HLR_SM_SHARE), so that product batches find room on every SM while solves run
+        self.solve_share = int(solve_share)
         # product batches on a high-priority stream: their CTAs are scheduled ahead of the
         # solves' kernels, so a short product does not queue behind long CG runs
         self.stream = torch.cuda.Stream(priority=-1)
@@ -312,7 +318,7 @@ class GpuBackend:
         with torch.cuda.stream(s):
             x = torch.zeros_like(r.x)
             r.iters, r.relres = A.solve_cg(r.x, x, rtol=r.rtol, maxit=r.maxit, acc=self.acc_cg, stream=s,
-                                           raise_noconv=False)
+                                           raise_noconv=False, sm_share=self.solve_share)
         s.synchronize()
         r.y = x
 

@@ -225,6 +225,44 @@ def test_unit_arrays_follow_the_oracle_unit_order(fmt, exp2d_case):
         assert afl.encode(a, prec[k], fmt).data == units[k].data
 
 
+def test_unit_list_precisions_sizes_and_errors(exp2d_case):
+    """hlr_unit_list: every lowrank column's precision is the oracle's APLR precision
+    eps sigma_0 / sigma_i (Section 3.3), dense leaves get eps (FP64 for MP); NULL outputs give
+    the sizes; short outputs and bad sigma are refused."""
+    import ctypes as C
+    from paper_2308_10960_gb300 import _binding as B
+    p, H, _ = exp2d_case
+    blocks = oracle_blocks(H)
+    vals, off, prec = hg.unit_arrays(blocks, H.eps, "afl")
+    expect = []
+    for b in H.blocks:
+        if b.kind == ohm.DENSE:
+            expect.append(H.eps)
+        elif b.rank:
+            us = afl.aplr_precisions(b.S, H.eps)
+            expect += list(us) + list(us)
+    assert np.array_equal(prec, np.array(expect))
+    assert off[-1] == vals.size == sum(b["D"].size if b["kind"] == ohm.DENSE else
+                                       b["S"].size * (b["nrows"] + b["ncols"]) for b in blocks)
+    _, _, prec_mp = hg.unit_arrays(blocks, H.eps, "mp")
+    dense = np.array([u for b in H.blocks for u in ([1] if b.kind == ohm.DENSE else [0] * (2 * b.rank))], bool)
+    assert np.all(prec_mp[dense] == 2.0 ** -60) and np.array_equal(prec_mp[~dense], prec[~dense])
+    db = hg._DescBuilder(p.n, None, blocks, H.eps, B.HLR_FMT_AFL_APLR)
+    nu, nv = C.c_int64(0), C.c_int64(0)
+    assert B.lib.hlr_unit_list(C.byref(db.desc), None, None, None, 0, 0, C.byref(nu), C.byref(nv)) == 0
+    assert nu.value == prec.size and nv.value == vals.size
+    small = np.zeros(nu.value, dtype=np.int64)
+    rc = B.lib.hlr_unit_list(C.byref(db.desc), small.ctypes.data, None, None, nu.value, 0, C.byref(nu), C.byref(nv))
+    assert rc == B.HLR_ERR_OOM
+    lr = next(i for i, b in enumerate(blocks) if b["kind"] != ohm.DENSE and b["S"].size > 1)
+    bad = [dict(b) for b in blocks]
+    bad[lr]["S"] = bad[lr]["S"][::-1].copy()          # not led by its maximum
+    with pytest.raises(hg.HlrError):
+        hg.unit_arrays(bad, H.eps, "afl")
+    with pytest.raises(hg.HlrError):
+        hg.unit_arrays(blocks, 0.0, "afl")
+
+
 def test_host_hmatrix_unit_arrays_match_block_copies():
     p = synth.laplace_problem(2048)
     Hh = hg.build_kernel_hmatrix(p.points, "laplace", 1e-6, diag=p.params["diag"])
