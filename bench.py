@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=262144)
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS comparison legs")
+    ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS/format/serve legs")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving leg")
     ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve", "small", "scale"],
                     help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
                          "uneven size with 1/8/32 right-hand sides in one batched launch sequence; serve: "
@@ -186,104 +187,90 @@ def multi_rhs_bytes(info: dict, n: int, r: int) -> float:
 
 
 # ------------------------------------------------------------------------------------------
-# oracle timing (cpu_baseline and the reference arm)
+# CPU baseline and the reference arm: the C oracle (oracle/cmatvec.c) on the host cores
 # ------------------------------------------------------------------------------------------
-def oracle_sample(n_sample: int = 4096, eps: float = 1e-6):
-    import synth
-    from oracle import hmatrix as ohm
-    p = synth.laplace_problem(n_sample)
-    H = ohm.build_hmatrix(p, eps, method="aca")
-    C = ohm.compress(H)
-    x = synth.rhs(n_sample, 1)
-    return C, x
-
-
-def _block_bytes(b) -> int:
-    from oracle import afl
-    return sum(afl.stream_bytes(u) + 16 for u in b.units) + 8 * b.rank
-
-
-def oracle_rate(C, x, budget_s: float, min_blocks: int = 1):
-    """Time the oracle's product over whole passes (or a budget-bounded prefix of blocks)."""
-    from oracle import matvec as omv
-    from oracle import hmatrix as ohm
-    nb = len(C.blocks)
-    done_bytes = 0
+def c_oracle_matrix(Hh, eps):
+    """The benchmark matrix compressed by the C oracle's own encoder (from the FP64 blocks the
+    host builder made; the oracle shares no code with the GPU library)."""
+    from oracle import cbaseline as cb
     t0 = time.perf_counter()
-    passes = 0
-    while True:
-        for i, (row0, c) in enumerate(omv.block_contributions(C, x)):
-            done_bytes += _block_bytes(C.blocks[i])
-            if time.perf_counter() - t0 > budget_s and i + 1 >= min_blocks:
-                break
-        else:
-            done_bytes += 32 * C.n
-            passes += 1
-            if time.perf_counter() - t0 < budget_s:
-                continue
-        break
-    dt = time.perf_counter() - t0
-    return done_bytes / dt / 1e9, dt, passes, done_bytes
+    M = cb.CMatrix(Hh.n, Hh.perm, Hh.block_views(), eps)
+    return M, time.perf_counter() - t0
 
 
-def cpu_baseline(args) -> dict:
-    C, x = oracle_sample(4096, args.eps)
-    gbs, dt, passes, nbytes = oracle_rate(C, x, budget_s=12.0)
-    return {"value": gbs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle product (AFL-APLR decode + exactly rounded FP64 sums, numpy, 1 thread) on the same "
-                      f"problem family at n=4096 (Fibonacci sphere, 1/(4 pi r), eps={args.eps:g}); "
-                      f"{passes} full passes + prefix in {dt:.1f} s, {nbytes} algorithmic bytes"}
+def c_oracle_rate(M, x, plain: bool, threads: int, reps: int, budget_s: float):
+    """Median GB/s of y += A~ x by the C oracle over up to `reps` products (fewer if one
+    product takes long, at least one), with the product's algorithmic bytes."""
+    y = np.zeros(M.n)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(reps):
+        y[:] = 0.0
+        t0 = time.perf_counter()
+        M.matvec(x, y, plain=plain, threads=threads)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_start > budget_s:
+            break
+    med = float(np.median(times))
+    return M.algorithmic_bytes(plain) / med / 1e9, med, len(times), y
+
+
+def cpu_baseline(args, Hh, x, y_ref) -> dict:
+    """The C oracle's compressed H-matvec (decoding on the fly) and its plain FP64 H-matvec over
+    the same matrix, on all host cores and on one core, median of 10 products (fewer on one
+    core when a product takes seconds)."""
+    M, t_enc = c_oracle_matrix(Hh, args.eps)
+    nproc = os.cpu_count() or 1
+    out = {}
+    for plain in (False, True):
+        key = "plain_fp64" if plain else "compressed"
+        gbs, med, k, y = c_oracle_rate(M, x, plain, nproc, 10, 20.0)
+        gbs1, med1, k1, _ = c_oracle_rate(M, x, plain, 1, 10, 20.0)
+        out[key] = {"GB/s_all_cores": gbs, "ms_all_cores": med * 1e3, "runs_all_cores": k,
+                    "GB/s_one_core": gbs1, "ms_one_core": med1 * 1e3, "runs_one_core": k1}
+        if not plain:
+            out[key]["rel_diff_vs_gpu_fp64"] = float(np.linalg.norm(y - y_ref) / np.linalg.norm(y_ref))
+    M.free()
+    c = out["compressed"]
+    return {"value": c["GB/s_all_cores"], "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": f"C oracle (oracle/cmatvec.c, OpenMP, decodes every unit when used; its own AFL-APLR "
+                      f"encoder) over the whole benchmark matrix (n={args.n}, eps={args.eps:g}), median of "
+                      f"{c['runs_all_cores']} products on {nproc} threads; encoding took {t_enc:.1f} s (untimed)",
+            "one_core": {"value": c["GB/s_one_core"], "runs": c["runs_one_core"]},
+            "plain_fp64": out["plain_fp64"], "compressed": c}
 
 
 def run_reference(args, world: int, rank: int):
+    """The reference arm: the C oracle's compressed product over the same workload on the host
+    cores (the matrix is built by the library's host builder and encoded by the oracle, both
+    untimed); each step is one whole product."""
     if rank != 0:
         return
-    C, x = oracle_sample(4096, args.eps)
-    from oracle import matvec as omv
-    blocks = C.blocks
-    nb = len(blocks)
-    # size a step so that warmup + steps fit in ~90 s
-    t0 = time.perf_counter()
-    probe = 0
-    for i, _ in enumerate(omv.block_contributions(C, x)):
-        probe += 1
-        if time.perf_counter() - t0 > 1.0:
-            break
-    per_block = (time.perf_counter() - t0) / probe
-    per_step = max(1, min(nb, int(90.0 / max(1, args.steps + args.warmup) / per_block)))
-    gen = iter(())
-    pos = 0
-
-    def step():
-        nonlocal gen, pos
-        bytes_ = 0
-        for _ in range(per_step):
-            try:
-                row0, c = next(gen)
-            except StopIteration:
-                gen = omv.block_contributions(C, x)
-                pos = 0
-                row0, c = next(gen)
-            bytes_ += _block_bytes(blocks[pos])
-            pos += 1
-        return bytes_
-
+    import synth
+    import paper_2308_10960_gb300 as hg
+    prob = synth.laplace_problem(args.n)
+    Hh = hg.build_kernel_hmatrix(prob.points, "laplace", args.eps, diag=prob.params["diag"], eta=2.0, leaf_size=64)
+    M, t_enc = c_oracle_matrix(Hh, args.eps)
+    x = synth.rhs(args.n, 1)
+    y = np.zeros(args.n)
+    nproc = os.cpu_count() or 1
     for _ in range(args.warmup):
-        step()
-    total = 0
+        M.matvec(x, y, threads=nproc)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        total += step()
+        M.matvec(x, y, threads=nproc)
     dt = time.perf_counter() - t0
-    v = total / dt / 1e9
-    sample = (f"oracle product on the same problem family at n=4096 (Fibonacci sphere, 1/(4 pi r), "
-              f"eps={args.eps:g}); each step = {per_step} consecutive blocks of the product, numpy, 1 thread")
+    v = M.algorithmic_bytes() * args.steps / dt / 1e9
+    sample = (f"C oracle (oracle/cmatvec.c, OpenMP on {nproc} threads) compressed H-matvec over the whole "
+              f"n={args.n}, eps={args.eps:g} matrix; each step one product")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(args, world),
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
+    M.free()
+    Hh.free()
     print(json.dumps(out), flush=True)
 
 
@@ -301,6 +288,94 @@ def time_loop(fn, steps: int, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
+
+
+def fp64_peak_tflops(dev) -> dict:
+    """Dense FP64 rate of this GPU, measured: cuBLAS DGEMM (torch.matmul, 4096^3) best of 5."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        a @ b
+    best = 1e30
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        e0.record()
+        a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return {"tflops": 2.0 * 4096 ** 3 / best / 1e12, "how": "torch.matmul float64 4096^3 (cuBLAS DGEMM), best of 5"}
+
+
+def kernel_table(A, info, n, stream, calls, step, peak_gbs, eps):
+    """Per-kernel CUDA-event times from a separate profiled loop of `calls` products (the timed
+    headline loop records no events) and the roofline of the dominant kernel."""
+    A.profile_read()
+    for _ in range(calls):
+        step(True)
+    kms, got = A.profile_read()
+    names = ["k_permute", "k_phase1<AFL32>", "k_phase2<AFL32>", "k_scatter"]
+    # algorithmic bytes per launch: x read + two permuted copies written (permute); phase 1 as
+    # hlr_info; phase 2 without the y and perm traffic that k_scatter does (8n y read, 8n y
+    # written, 8n perm; phase 2 writes its row totals, 8n, which are not algorithmic)
+    kb = [16.0 * n, float(info["phase1_bytes"]), float(info["phase2_bytes"]) - 24.0 * n, 24.0 * n]
+    avg = [m / max(got, 1) for m in kms]
+    dom = int(np.argmax(avg))
+    achieved = kb[dom] / (avg[dom] / 1e3) / 1e9
+    tr = recorded_traffic(names[dom], kb[dom], eps)
+    return {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak_gbs["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peak_gbs["hbm_gbs"], "traffic": tr,
+            "peak_source": f"{peak_gbs['source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+            "algorithmic_bytes_per_launch": kb[dom],
+            "kernel_ms_avg": dict(zip(names, avg)), "kernel_share": dict(zip(names, [m / max(sum(avg), 1e-12) for m in avg])),
+            "profiled_products": got,
+            "kernel_GB/s": {nm: (b / (t / 1e3) / 1e9 if t > 0 else None) for nm, b, t in zip(names, kb, avg)}}
+
+
+def serve_leg(dev, eps: float) -> dict:
+    """A short served run: 6 resident Matern matrices (n 16384 .. 65536), 60 Poisson requests at
+    200 requests/s, 30 % CG solves to a relative residual of 1e-8: p50/p99 latency per kind."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+    from paper_2308_10960_gb300 import serve
+    sizes = [int(round(16384 * 4.0 ** (i / 5))) for i in range(6)]
+    host = {}
+    for i, n in enumerate(sizes):
+        p = synth.matern_problem(n, seed=200 + i)
+        host[f"m{i}"] = hg.build_kernel_hmatrix(p.points, "matern15", eps, scale=p.params["scale"], diag=p.params["diag"])
+    be = serve.GpuBackend(host)
+    names = sorted(host, key=lambda m: int(m[1:]))
+    srv = serve.Server(be, budget_bytes=int(150e9), cg_workers=4, max_rhs=32)
+    srv.preload(names)
+    warm = []
+    for i, m in enumerate(names):
+        xw = torch.from_numpy(synth.rhs(host[m].n, 9000 + i)).to(dev)
+        warm.append(serve.Request(-1 - 2 * i, "matvec", m, xw, arrival=0.0))
+        warm.append(serve.Request(-2 - 2 * i, "solve", m, xw, arrival=0.0, rtol=1e-8, maxit=3))
+    torch.cuda.synchronize()
+    srv.run(warm, realtime=False)
+    g = np.random.default_rng(6)
+    arr = serve.poisson_arrivals(60, 200.0, 5)
+    reqs = []
+    for i in range(60):
+        m = names[int(g.integers(len(names)))]
+        kind = "solve" if g.random() < 0.3 else "matvec"
+        x = torch.from_numpy(synth.rhs(host[m].n, 7000 + i)).to(dev)
+        reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000))
+    torch.cuda.synchronize()
+    st = srv.run(reqs).as_dict()
+    be.close()
+    for h in host.values():
+        h.free()
+    lat = st["latency_ms"]
+    return {"workload": f"6 resident Matern nu=1.5 matrices n {sizes[0]}..{sizes[-1]}, eps={eps:g}, 60 Poisson "
+                        f"requests at 200/s, 30% CG solves to 1e-8",
+            "products_ms": lat.get("matvec"), "solves_ms": lat.get("solve"), "requests_per_s": st["requests_per_s"],
+            "GB/s": st["GB/s"], "failed": st["failed"],
+            "cg_true_relres_max": float(max([r.relres for r in reqs if r.kind == "solve"] or [0]))}
 
 
 def run_ours(args, world: int, rank: int, local: int):
@@ -321,48 +396,57 @@ def run_ours(args, world: int, rank: int, local: int):
     stream = torch.cuda.current_stream(dev)
     bytes_step = float(info["algorithmic_bytes"])
 
-    def step32():
-        A.matvec(x, y, acc="fp32", stream=stream, profile=True)
+    def step32(profile=False):
+        A.matvec(x, y, acc="fp32", stream=stream, profile=profile)
 
-    for _ in range(args.warmup):
-        A.matvec(x, y, acc="fp32", stream=stream)
+    for _ in range(max(3, args.warmup)):
+        step32()
     torch.cuda.synchronize()
-    A.profile_read()
     clocks = ClockSampler(local)
     clocks.start()
     barrier(world)
-    el = time_loop(step32, args.steps, stream)
+    el = time_loop(step32, args.steps, stream)       # the headline: no events inside the loop
     barrier(world)
     clk = clocks.stop()
     A.check()
-    kms, calls = A.profile_read()
     el_max, total_bytes = aggregate(el, bytes_step * args.steps, world)
     value = total_bytes / el_max / 1e9
     ms_step = el_max / args.steps * 1e3
-
-    # per-kernel roofline (dominant kernel by time)
     peaks = measured_peaks()
-    k_names = ["k_permute", "k_phase1<AFL32>", "k_phase2<AFL32>"]
-    k_bytes = [16.0 * args.n, float(info["phase1_bytes"]), float(info["phase2_bytes"])]
-    share = [m / max(sum(kms), 1e-12) for m in kms]
-    dom = int(np.argmax(kms))
-    avg_ms = kms[dom] / max(calls, 1)
-    achieved = k_bytes[dom] / (avg_ms / 1e3) / 1e9
-    tr = recorded_traffic(k_names[dom], k_bytes[dom], args.eps)
-    roofline = {"bound": "hbm", "kernel": k_names[dom], "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": tr,
-                "peak_source": f"{peaks['source']} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": k_bytes[dom],
-                "kernel_ms_avg": {k: m / max(calls, 1) for k, m in zip(k_names, kms)},
-                "kernel_share": dict(zip(k_names, share))}
+    roofline = kernel_table(A, info, args.n, stream, min(200, max(20, args.steps)), step32, peaks, args.eps)
 
     extra = {}
+    y64 = None
     if not args.quick:
-        steps_cmp = max(50, args.steps // 4)
+        steps_cmp = max(20, min(200, args.steps // 4))
 
-        def step64():
-            A.matvec(x, y, acc="fp64", stream=stream)
+        def step64(profile=False):
+            A.matvec(x, y, acc="fp64", stream=stream, profile=profile)
+        for _ in range(3):
+            step64()
         el64 = time_loop(step64, steps_cmp, stream)
+        A.profile_read()
+        for _ in range(10):
+            step64(True)
+        kms64, c64 = A.profile_read()
+        t64 = el64 / steps_cmp
+        f64 = fp64_peak_tflops(dev)
+        yv = torch.zeros(args.n, dtype=torch.float64, device=dev)
+        A.matvec(x, yv, acc="fp64", stream=stream)
+        torch.cuda.synchronize()
+        y64 = yv.cpu().numpy()
+        values = float(info["values"])
+        ph2_64 = kms64[2] / max(c64, 1)
+        extra["afl_fp64_acc"] = {
+            "ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9,
+            "kernel_ms_avg": {"k_permute": kms64[0] / max(c64, 1), "k_phase1<AFL64>": kms64[1] / max(c64, 1),
+                              "k_phase2<AFL64>": ph2_64},
+            "roofline": {"bound": "fp64", "achieved": 2.0 * values / t64 / 1e12, "peak": f64["tflops"],
+                         "unit": "TFLOP/s", "frac": 2.0 * values / t64 / 1e12 / f64["tflops"],
+                         "peak_source": "measured here: " + f64["how"],
+                         "note": "one FP64 multiply-add per decoded value is the product's algorithmic FP64 work",
+                         "hbm": {"achieved": bytes_step / t64 / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": bytes_step / t64 / 1e9 / peaks["hbm_gbs"]}}}
         Ap = Hh.upload("fp64")
         infp = Ap.info
 
@@ -370,10 +454,9 @@ def run_ours(args, world: int, rank: int, local: int):
             Ap.matvec(x, y, acc="fp64", stream=stream)
         for _ in range(3):
             stepp()
-        elp = time_loop(stepp, steps_cmp, stream)
+        tp = time_loop(stepp, steps_cmp, stream) / steps_cmp
+        Ap.free()
         t32 = el / args.steps
-        t64 = el64 / steps_cmp
-        tp = elp / steps_cmp
         multi = {}
         for r in (8, 32):
             X = torch.from_numpy(synth.rhs(args.n * r, 2 + r)).to(dev).view(r, args.n)
@@ -427,25 +510,23 @@ def run_ours(args, world: int, rank: int, local: int):
                   "rejected_units": rejected, "vs_build_time": te / t_build}
         del v_d, o_d, u_d
         torch.cuda.empty_cache()
-        extra = {
+        extra.update({
             "encode_device": encode,
             "formats": formats,
             "multi_rhs": multi,
-            "afl_fp64_acc": {"ms_per_step": t64 * 1e3, "GB/s": bytes_step / t64 / 1e9},
             "plain_fp64": {"ms_per_step": tp * 1e3, "GB/s": infp["algorithmic_bytes"] / tp / 1e9,
                            "algorithmic_bytes": infp["algorithmic_bytes"],
                            "pct_hbm": infp["algorithmic_bytes"] / tp / 1e9 / peaks["hbm_gbs"]},
             "speedup_vs_plain_fp64": tp / t32,
             "speedup_fp64acc_vs_plain_fp64": tp / t64,
-        }
-        Ap.free()
+        })
 
     # end to end through the C-ABI call with host buffers
     xh = torch.from_numpy(synth.rhs(args.n, 1)).pin_memory()
     yh = torch.zeros(args.n, dtype=torch.float64).pin_memory()
     for _ in range(3):
         A.matvec_host(xh, yh, acc="fp32", stream=stream)
-    steps_e2e = max(50, args.steps // 4)
+    steps_e2e = max(50, min(500, args.steps // 4))
     t0 = time.perf_counter()
     for _ in range(steps_e2e):
         A.matvec_host(xh, yh, acc="fp32", stream=stream)
@@ -457,7 +538,15 @@ def run_ours(args, world: int, rank: int, local: int):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+        if y64 is None:
+            yv = torch.zeros(args.n, dtype=torch.float64, device=dev)
+            A.matvec(x, yv, acc="fp64", stream=stream)
+            torch.cuda.synchronize()
+            y64 = yv.cpu().numpy()
+        cpu = cpu_baseline(args, Hh, x.cpu().numpy(), y64)
+    serving = None
+    if rank == 0 and not args.quick and not args.no_serve:
+        serving = serve_leg(dev, 1e-6)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -466,6 +555,8 @@ def run_ours(args, world: int, rank: int, local: int):
                "pct_hbm_peak": value / world / peaks["hbm_gbs"], "pct_hbm_8tbs_spec": value / world / 8000.0,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(info["launches"]) * args.steps,
+               "p99_solve_ms": (serving or {}).get("solves_ms", {}) and serving["solves_ms"].get("p99"),
+               "serve": serving,
                "matrix": {"nblocks": info["nblocks"], "rank_sum": info["rank_sum"],
                           "compressed_bytes": info["stream_bytes"] + info["header_bytes"] + 8 * info["rank_sum"],
                           "fp64_bytes": info["fp64_bytes"],
