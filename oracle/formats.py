@@ -28,7 +28,3 @@ def dynamic_range(e: int, m: int) -> int:
     log2_ratio = math.log2(2.0 - 2.0 ** (-m)) + bias - (1 - bias - m)
     return math.floor(log2_ratio * math.log10(2.0))
 
-
-def afl_dynamic_range(e: int) -> float:
-    """Dynamic range log10(2^(2^e)) reached with e exponent bits (footnote to Section 3.2)."""
-    return (2 ** e) * math.log10(2.0)

@@ -538,17 +538,36 @@ uint64_t fnv1a(const uint8_t *p, size_t n) {
   return h;
 }
 
+// Streams the file through a small buffer, hashing every byte it writes (FNV-1a, updated as it
+// goes), so that saving needs no second copy of the matrix.
 struct Writer {
+  FILE *f;
+  uint64_t h = 1469598103934665603ull;
+  bool ok = true;
   std::vector<uint8_t> buf;
+  explicit Writer(FILE *file) : f(file) { buf.reserve(1 << 20); }
+  void write(const void *src, size_t n) {
+    const uint8_t *p = static_cast<const uint8_t *>(src);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= p[i];
+      h *= 1099511628211ull;
+    }
+    if (buf.size() + n > buf.capacity()) flush();
+    if (n >= buf.capacity()) {
+      ok = ok && std::fwrite(p, 1, n, f) == n;
+    } else {
+      buf.insert(buf.end(), p, p + n);
+    }
+  }
+  void flush() {
+    if (!buf.empty()) ok = ok && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    buf.clear();
+  }
   template <typename T>
   void put(const T &v) {
-    const uint8_t *p = reinterpret_cast<const uint8_t *>(&v);
-    buf.insert(buf.end(), p, p + sizeof(T));
+    write(&v, sizeof(T));
   }
-  void put_doubles(const std::vector<double> &v) {
-    const uint8_t *p = reinterpret_cast<const uint8_t *>(v.data());
-    buf.insert(buf.end(), p, p + 8 * v.size());
-  }
+  void put_doubles(const std::vector<double> &v) { write(v.data(), 8 * v.size()); }
 };
 
 struct Reader {
@@ -578,14 +597,19 @@ struct Reader {
 
 extern "C" int hlr_host_save(const hlr_host_hmatrix *hm, const char *path) {
   if (!hm || !path) return set_error(HLR_ERR_INVALID, "hlr_host_save: null argument");
-  Writer w;
-  w.buf.insert(w.buf.end(), kMagic, kMagic + 8);
+  // written to path.tmp and renamed over path once complete, so a failed save leaves an
+  // earlier file at path as it was
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE *f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: cannot open ") + tmp);
+  Writer w(f);
+  w.write(kMagic, 8);
   w.put(kVersion);
   w.put(uint32_t(0));
   w.put(int64_t(hm->n));
   w.put(int64_t(hm->blocks.size()));
   w.put(hm->eps);
-  for (int64_t v : hm->perm) w.put(v);
+  w.write(hm->perm.data(), 8 * hm->perm.size());
   for (const auto &B : hm->blocks) {
     w.put(B.row0);
     w.put(B.nrows);
@@ -601,12 +625,14 @@ extern "C" int hlr_host_save(const hlr_host_hmatrix *hm, const char *path) {
       w.put_doubles(B.X);
     }
   }
-  w.put(fnv1a(w.buf.data(), w.buf.size()));
-  FILE *f = std::fopen(path, "wb");
-  if (!f) return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: cannot open ") + path);
-  const size_t put = std::fwrite(w.buf.data(), 1, w.buf.size(), f);
+  const uint64_t h = w.h;
+  w.flush();
+  const bool wrote = w.ok && std::fwrite(&h, 1, 8, f) == 8;
   const int cl = std::fclose(f);
-  if (put != w.buf.size() || cl != 0) return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: write failed: ") + path);
+  if (!wrote || cl != 0 || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return set_error(HLR_ERR_INVALID, std::string("hlr_host_save: write failed: ") + path);
+  }
   return HLR_OK;
 }
 
@@ -615,11 +641,17 @@ extern "C" int hlr_host_load(const char *path, hlr_host_hmatrix **out) {
   *out = nullptr;
   FILE *f = std::fopen(path, "rb");
   if (!f) return set_error(HLR_ERR_INVALID, std::string("hlr_host_load: cannot open ") + path);
-  std::vector<uint8_t> buf;
-  uint8_t chunk[1 << 16];
-  size_t got;
-  while ((got = std::fread(chunk, 1, sizeof(chunk), f)) > 0) buf.insert(buf.end(), chunk, chunk + got);
+  // one read into a buffer of the file's size
+  long size = -1;
+  if (std::fseek(f, 0, SEEK_END) == 0) size = std::ftell(f);
+  if (size < 0 || std::fseek(f, 0, SEEK_SET) != 0) {
+    std::fclose(f);
+    return set_error(HLR_ERR_INVALID, std::string("hlr_host_load: cannot size ") + path);
+  }
+  std::vector<uint8_t> buf(static_cast<size_t>(size));
+  const size_t got = size > 0 ? std::fread(buf.data(), 1, buf.size(), f) : 0;
   std::fclose(f);
+  if (got != buf.size()) return set_error(HLR_ERR_INVALID, std::string("hlr_host_load: read failed: ") + path);
   if (buf.size() < 8 + 4 + 4 + 8 + 8 + 8 + 8 || std::memcmp(buf.data(), kMagic, 8) != 0)
     return set_error(HLR_ERR_INVALID, "hlr_host_load: not a saved H-matrix");
   const size_t body = buf.size() - 8;

@@ -308,13 +308,39 @@ def test_host_checkpoint_round_trip_and_corruption(tmp_path):
     bad.append(bytes(flipped))
     bad.append(raw[:-100])
     bad.append(b"XXXXXXXX" + raw[8:])
-    ver = bytearray(raw)
-    ver[8] = 2
-    bad.append(bytes(ver))
     for k, data in enumerate(bad):
         q = str(tmp_path / f"bad{k}.hlr")
         open(q, "wb").write(data)
         with pytest.raises(hg.HlrError):
             hg.load_host_hmatrix(q)
+
+    def fnv1a(b):                      # the file's trailer: FNV-1a 64 of every byte before it
+        h = 1469598103934665603
+        for c in b:
+            h = ((h ^ c) * 1099511628211) & (2 ** 64 - 1)
+        return h.to_bytes(8, "little")
+
+    body = bytearray(raw[:-8])
+    assert fnv1a(bytes(body)) == raw[-8:]
+    ver = bytearray(body)
+    ver[8] = 2                          # another version, with a valid hash
+    q = str(tmp_path / "ver.hlr")
+    open(q, "wb").write(bytes(ver) + fnv1a(bytes(ver)))
+    with pytest.raises(hg.HlrError, match="unsupported version"):
+        hg.load_host_hmatrix(q)
+    bad_blk = bytearray(body)
+    off = 8 + 4 + 4 + 8 + 8 + 8 + 8 * 1500   # first block: row0
+    bad_blk[off:off + 8] = (1500).to_bytes(8, "little", signed=True)   # rows past n
+    q = str(tmp_path / "blk.hlr")
+    open(q, "wb").write(bytes(bad_blk) + fnv1a(bytes(bad_blk)))
+    with pytest.raises(hg.HlrError, match="malformed"):
+        hg.load_host_hmatrix(q)
+    # a failed save (unwritable directory) leaves no partial file and raises
+    with pytest.raises(hg.HlrError):
+        Hh2 = hg.build_kernel_hmatrix(p.points[:200], "laplace", 1e-6, diag=p.params["diag"])
+        try:
+            Hh2.save(str(tmp_path / "missing_dir" / "m.hlr"))
+        finally:
+            Hh2.free()
     with pytest.raises(hg.HlrError):
         hg.load_host_hmatrix(str(tmp_path / "missing.hlr"))

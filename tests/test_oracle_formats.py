@@ -27,8 +27,3 @@ def test_table2_dynamic_range():
     for name, e, m, printed in _rows("table2_dynamic_range.txt"):
         assert formats.dynamic_range(int(e), int(m)) == int(printed), name
 
-
-def test_afl_exponent_dynamic_range_footnote():
-    # footnote of Section 3.2: e exponent bits reach a dynamic range of log10(2^(2^e))
-    assert math.isclose(formats.afl_dynamic_range(3), 8 * math.log10(2))
-    assert math.isclose(formats.afl_dynamic_range(11), 2048 * math.log10(2))
