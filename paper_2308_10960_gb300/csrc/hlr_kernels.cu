@@ -457,9 +457,13 @@ __global__ void k_scatter(const __grid_constant__ Jobs<NB> J) {
 // Producer: TMA bulk copies of the CTA's pieces and their multipliers into the slot ring
 // ---------------------------------------------------------------------------------------------
 // Issue the TMA copies of one product's pieces for this CTA (entries [e0, e1) of its issue
-// stream). i counts the pieces this CTA issued during the launch (ring slot i % kStages) and
-// cur is the slot of the latest one. The multi-RHS kernels (R > 1) skip the aux copies.
-// Returns false when a wait for a free slot gave up (status bit 2 set).
+// stream). The stream is read 32 entries per coalesced load, one load ahead, and lane k holds
+// entry k: the piece entries are taken in order by lane 0 (wait for the slot, post the bytes the
+// slot expects, copy the piece), and the aux entries (multiplier ranges) that follow a piece are
+// issued by their own lanes at once into that piece's slot. i counts the pieces this CTA issued
+// during the launch (ring slot i % kStages) and cur is the slot of the latest one. The multi-RHS
+// kernels (R > 1) skip the aux copies. Returns false when a wait for a free slot gave up
+// (status bit 2 set).
 template <int FMT, int PH, int R>
 __device__ bool produce(const DevLayout &L, uint32_t e0, uint32_t e1, uint8_t *smem, uint64_t *full,
                         uint64_t *empty, uint32_t &i, uint32_t &cur) {
@@ -473,36 +477,45 @@ __device__ bool produce(const DevLayout &L, uint32_t e0, uint32_t e1, uint8_t *s
   const uint8_t *fsrc = kFP32<FMT> ? reinterpret_cast<const uint8_t *>(L.fac32)
                                          : reinterpret_cast<const uint8_t *>(L.fac64);
   const uint4 *ent = reinterpret_cast<const uint4 *>(L.ph[PH].ent);
-  // the stream is read 32 entries per coalesced load, one load ahead
+  // this lane's aux entry into slot `sl` (lane of an aux entry only)
+  auto aux_copy = [&](const uint4 &en, uint32_t sl) {
+    const uint32_t nelem = en.y & 0xffffu, which = en.y >> 16;
+    const uint8_t *src = (which == 0 ? xsrc : which == 1 ? tsrc : fsrc) + size_t(en.x) * esz;
+    tma_load(smem + size_t(sl) * slot + kPieceMax + kSlotPad + size_t(en.z) * esz, src, nelem * esz, &full[sl]);
+  };
   uint4 nxt = e0 + lane < e1 ? __ldg(ent + e0 + lane) : make_uint4(0, 0, 0, 0);
   for (uint32_t e = e0; e < e1; e += 32) {
     const uint4 mine = nxt;
     if (e + 32 + lane < e1) nxt = __ldg(ent + e + 32 + lane);
     const uint32_t cnt = min(32u, e1 - e);
-    for (uint32_t k = 0; k < cnt; ++k) {
-      const uint32_t a = __shfl_sync(kFull, mine.x, k), b = __shfl_sync(kFull, mine.y, k);
-      const uint32_t c = __shfl_sync(kFull, mine.z, k), d = __shfl_sync(kFull, mine.w, k);
-      if (b & kIssuePiece) {
-        const uint32_t s = i % kStages;
-        uint32_t good = 1;
-        if (lane == 0) {
-          if (i >= uint32_t(kStages) && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
-            atomicOr(L.status, 2u);
-            good = 0;
-          } else {
-            const uint64_t off = (uint64_t(b & ~kIssuePiece) << 32) | a;
-            mbar_expect_tx(&full[s], R == 1 ? c + d * esz : c);
-            tma_load(smem + size_t(s) * slot, L.base + off, c, &full[s]);
-          }
+    const bool valid = uint32_t(lane) < cnt;
+    const bool is_piece = valid && (mine.y & kIssuePiece);
+    uint32_t pmask = __ballot_sync(kFull, is_piece);
+    // aux entries continuing the latest piece of the previous batch
+    const uint32_t first = pmask ? uint32_t(__ffs(pmask) - 1) : cnt;
+    if (R == 1 && valid && !is_piece && uint32_t(lane) < first) aux_copy(mine, cur);
+    while (pmask) {
+      const uint32_t p = __ffs(pmask) - 1;
+      pmask &= pmask - 1;
+      const uint32_t next = pmask ? uint32_t(__ffs(pmask) - 1) : cnt;
+      const uint32_t a = __shfl_sync(kFull, mine.x, p), b = __shfl_sync(kFull, mine.y, p);
+      const uint32_t c = __shfl_sync(kFull, mine.z, p), d = __shfl_sync(kFull, mine.w, p);
+      const uint32_t s = i % kStages;
+      uint32_t good = 1;
+      if (lane == 0) {
+        if (i >= uint32_t(kStages) && !mbar_wait(&empty[s], ((i / kStages) - 1) & 1)) {
+          atomicOr(L.status, 2u);
+          good = 0;
+        } else {
+          const uint64_t off = (uint64_t(b & ~kIssuePiece) << 32) | a;
+          mbar_expect_tx(&full[s], R == 1 ? c + d * esz : c);
+          tma_load(smem + size_t(s) * slot, L.base + off, c, &full[s]);
         }
-        if (!__shfl_sync(kFull, good, 0)) return false;
-        cur = s;
-        ++i;
-      } else if (R == 1 && lane == 0) {
-        const uint32_t nelem = b & 0xffffu, which = b >> 16;
-        const uint8_t *src = (which == 0 ? xsrc : which == 1 ? tsrc : fsrc) + size_t(a) * esz;
-        tma_load(smem + size_t(cur) * slot + kPieceMax + kSlotPad + size_t(c) * esz, src, nelem * esz, &full[cur]);
       }
+      if (!__shfl_sync(kFull, good, 0)) return false;
+      cur = s;
+      ++i;
+      if (R == 1 && uint32_t(lane) > p && uint32_t(lane) < next) aux_copy(mine, cur);
     }
   }
   return true;
