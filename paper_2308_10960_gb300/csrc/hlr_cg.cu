@@ -142,9 +142,16 @@ struct Cg {
     k_dot<<<kDotBlocks, kDotThreads, 0, st>>>(a, c, n, W.partial);
     k_dot_final<<<1, kDotThreads, 0, st>>>(W.partial, W.scal + slot);
   }
+  // the scalars, and the handle's status words: a product kernel that gave up a bounded wait
+  // has left an incomplete product, so the solve stops with HLR_ERR_TIMEOUT
   int fetch() {
+    uint32_t status[4] = {0, 0, 0, 0};
     int rc = ck(cudaMemcpyAsync(h_scal, W.scal, sizeof(h_scal), cudaMemcpyDeviceToHost, st), "hlr_solve_cg");
+    if (!rc) rc = ck(cudaMemcpyAsync(status, H.L.status, sizeof(status), cudaMemcpyDeviceToHost, st), "hlr_solve_cg");
     if (!rc) rc = ck(cudaStreamSynchronize(st), "hlr_solve_cg");
+    if (!rc && (status[0] | status[1] | status[2] | status[3]))
+      rc = set_error(HLR_ERR_TIMEOUT, "hlr_solve_cg: a product kernel gave up a bounded wait (status " +
+                                          std::to_string(status[0]) + ")");
     return rc;
   }
   // ||rhs - A sol|| with the FP64-accumulation product; the residual is left in W.rt

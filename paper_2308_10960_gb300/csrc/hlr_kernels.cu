@@ -134,6 +134,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
+// A consumer warp hands its ring slot back to the producer (empty barrier, one arrival per warp).
+// The lanes read the slot with ordinary shared loads (the generic proxy) and the next TMA copy
+// writes it through the async proxy: each lane's proxy fence orders its reads before the copy
+// the producer issues after its wait, without which a copy can overtake reads still in flight
+// (observed: the first rows of a leaf decoding the next piece's bytes, when other kernels share
+// the SMs).
+__device__ __forceinline__ void release_slot(uint64_t *b) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(b);
+}
 // try_wait with a suspend-time hint: a waiting warp sleeps (up to ~20 us per try) until the
 // phase completes instead of spinning on issue slots
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *b, uint32_t parity) {
@@ -675,8 +686,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
         L.partial[size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk] = double(dot);
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -771,8 +781,7 @@ __device__ bool consume_phase1_pairs(const DevLayout &L, uint32_t np, uint32_t &
       else
         L.partial[size_t(sg.x.pbase) + size_t(h.j) * sg.x.nchunks + sg.x.chunk] = double(dot);
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -951,8 +960,7 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
       }
       parity ^= 1u;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -1041,8 +1049,7 @@ __device__ bool consume_phase2_pairs(const DevLayout &L, uint32_t np, uint32_t &
     }
     // the slot is not read after this point: hand it back before the leaf's reduction
     const uint32_t row0 = ph->row0;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
     if (flags & PF_END_LEAF) {
       // reduce-scatter over the warp (as consume_phase2_reg): lane l ends with rows 2l, 2l + 1
 #pragma unroll
@@ -1177,8 +1184,7 @@ __device__ bool consume_phase2_f64(const DevLayout &L, uint32_t np, uint32_t &it
     }
     // the slot is not read after this point: hand it back before the leaf's reduction
     const uint32_t row0 = ph->row0;
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
     if (flags & PF_END_LEAF) {
 #pragma unroll
       for (int st = 0; st < 5; ++st) {
@@ -1285,8 +1291,7 @@ __device__ bool consume_phase1_f64(const DevLayout &L, uint32_t np, uint32_t &it
       else
         L.partial[size_t(sg.x.pbase) + size_t(h.j) * sg.x.nchunks + sg.x.chunk] = dot;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -1409,8 +1414,7 @@ __device__ bool consume_phase2(const DevLayout &L, uint32_t np, uint32_t &it, ui
       }
       parity ^= 1u;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -1477,8 +1481,7 @@ __device__ bool consume_phase2_rows(const DevLayout &L, uint32_t np, uint32_t &i
       }
       parity ^= 1u;
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -1568,8 +1571,7 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
         for (int q = 0; q < kRB; ++q) dst[q] = double(acc[q]);
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
@@ -1726,8 +1728,7 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
       }
       bar_consumers();
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[s]);
+    release_slot(&empty[s]);
   }
   return true;
 }
