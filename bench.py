@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the FP64/plain/multi-RHS/format/serve legs")
     ap.add_argument("--no-serve", action="store_true", help="skip the short serving leg")
+    ap.add_argument("--acc", default="fp32", choices=["fp32", "fp64"],
+                    help="accumulation of the headline product: fp32 in-block / fp64 across blocks (default), "
+                         "or fp64 throughout (the paper's arithmetic)")
     ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve", "small", "scale"],
                     help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
                          "uneven size with 1/8/32 right-hand sides in one batched launch sequence; serve: "
@@ -61,7 +64,8 @@ def parse():
 
 
 def workload_config(args, world: int) -> dict:
-    return {"workload": f"laplace-sphere n={args.n} eps={args.eps:g} AFL-APLR, FP32 in-block / FP64 cross-block",
+    accs = "FP32 in-block / FP64 cross-block" if getattr(args, "acc", "fp32") == "fp32" else "FP64 throughout"
+    return {"workload": f"laplace-sphere n={args.n} eps={args.eps:g} AFL-APLR, {accs}",
             "n": args.n, "eps": args.eps, "kernel": "1/(4 pi r), diag = mean row sum", "points": "fibonacci sphere",
             "leaf_size": 64, "eta": 2.0, "lowrank": "ACA + SVD recompression", "rhs": 1,
             "l2": "inputs larger than L2 (compressed matrix ~1.6 GB >> 129 MB)",
@@ -309,14 +313,15 @@ def fp64_peak_tflops(dev) -> dict:
     return {"tflops": 2.0 * 4096 ** 3 / best / 1e12, "how": "torch.matmul float64 4096^3 (cuBLAS DGEMM), best of 5"}
 
 
-def kernel_table(A, info, n, stream, calls, step, peak_gbs, eps):
+def kernel_table(A, info, n, stream, calls, step, peak_gbs, eps, acc="fp32"):
     """Per-kernel CUDA-event times from a separate profiled loop of `calls` products (the timed
     headline loop records no events) and the roofline of the dominant kernel."""
     A.profile_read()
     for _ in range(calls):
         step(True)
     kms, got = A.profile_read()
-    names = ["k_permute", "k_phase1<AFL32>", "k_phase2<AFL32>", "k_scatter"]
+    tag = "AFL32" if acc == "fp32" else "AFL64"
+    names = ["k_permute", f"k_phase1<{tag}>", f"k_phase2<{tag}>", "k_scatter"]
     # algorithmic bytes per launch: x read + two permuted copies written (permute); phase 1 as
     # hlr_info; phase 2 without the y and perm traffic that k_scatter does (8n y read, 8n y
     # written, 8n perm; phase 2 writes its row totals, 8n, which are not algorithmic)
@@ -359,21 +364,31 @@ def serve_leg(dev, eps: float) -> dict:
     srv.run(warm, realtime=False)
     g = np.random.default_rng(6)
     arr = serve.poisson_arrivals(60, 200.0, 5)
-    reqs = []
+    plan = []
     for i in range(60):
         m = names[int(g.integers(len(names)))]
-        kind = "solve" if g.random() < 0.3 else "matvec"
-        x = torch.from_numpy(synth.rhs(host[m].n, 7000 + i)).to(dev)
-        reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000))
+        plan.append((i, "solve" if g.random() < 0.3 else "matvec", m, arr[i]))
+    xs = {i: torch.from_numpy(synth.rhs(host[m].n, 7000 + i)).to(dev) for i, _, m, _ in plan}
+
+    def requests(kinds):
+        return [serve.Request(i, k, m, xs[i], arrival=a, rtol=1e-8, maxit=50000) for i, k, m, a in plan if k in kinds]
+    # the same product requests at the same arrival times with no solves running: the latency
+    # a product has alone, against which the mixed run's product latency is read
+    torch.cuda.synchronize()
+    alone = srv.run(requests(("matvec",))).as_dict()["latency_ms"].get("matvec")
+    reqs = requests(("matvec", "solve"))
     torch.cuda.synchronize()
     st = srv.run(reqs).as_dict()
     be.close()
     for h in host.values():
         h.free()
     lat = st["latency_ms"]
+    prod = lat.get("matvec")
     return {"workload": f"6 resident Matern nu=1.5 matrices n {sizes[0]}..{sizes[-1]}, eps={eps:g}, 60 Poisson "
                         f"requests at 200/s, 30% CG solves to 1e-8",
-            "products_ms": lat.get("matvec"), "solves_ms": lat.get("solve"), "requests_per_s": st["requests_per_s"],
+            "products_ms": prod, "products_alone_ms": alone,
+            "products_p99_vs_alone": (prod["p99"] / alone["p99"]) if prod and alone else None,
+            "solves_ms": lat.get("solve"), "requests_per_s": st["requests_per_s"],
             "GB/s": st["GB/s"], "failed": st["failed"],
             "cg_true_relres_max": float(max([r.relres for r in reqs if r.kind == "solve"] or [0]))}
 
@@ -397,7 +412,7 @@ def run_ours(args, world: int, rank: int, local: int):
     bytes_step = float(info["algorithmic_bytes"])
 
     def step32(profile=False):
-        A.matvec(x, y, acc="fp32", stream=stream, profile=profile)
+        A.matvec(x, y, acc=args.acc, stream=stream, profile=profile)
 
     for _ in range(max(3, args.warmup)):
         step32()
@@ -413,7 +428,7 @@ def run_ours(args, world: int, rank: int, local: int):
     value = total_bytes / el_max / 1e9
     ms_step = el_max / args.steps * 1e3
     peaks = measured_peaks()
-    roofline = kernel_table(A, info, args.n, stream, min(200, max(20, args.steps)), step32, peaks, args.eps)
+    roofline = kernel_table(A, info, args.n, stream, min(200, max(20, args.steps)), step32, peaks, args.eps, args.acc)
 
     extra = {}
     y64 = None
@@ -471,6 +486,22 @@ def run_ours(args, world: int, rank: int, local: int):
             bm = multi_rhs_bytes(info, args.n, r)
             multi[str(r)] = {"ms_per_step": tm * 1e3, "GB/s": bm / tm / 1e9, "algorithmic_bytes": bm,
                              "speedup_vs_r_single_products": r * t32 / tm}
+            if r == 32:
+                # FP64 accumulation of 32 columns: 32 single-RHS FP64 products in one batched launch,
+                # beside the floor of any FP64 contraction of the decoded values at the measured
+                # DGEMM rate (2 r flops per value)
+                def stepm64():
+                    hg.matvec_batched([A], [X], [Y], acc="fp64", stream=stream)
+                for _ in range(3):
+                    stepm64()
+                km64 = max(3, km // 4)
+                tm64 = time_loop(stepm64, km64, stream) / km64
+                floor = 2.0 * r * float(info["values"]) / (f64["tflops"] * 1e12)
+                multi["32_fp64"] = {"ms_per_step": tm64 * 1e3, "vs_32_fp64_single_products": r * t64 / tm64,
+                                    "vs_fp32_pass": tm64 / tm,
+                                    "dgemm_rate_floor_ms": floor * 1e3,
+                                    "note": "floor = 2 x 32 x decoded values / measured DGEMM rate: no FP64 "
+                                            "contraction of the decoded values runs faster than that rate"}
             del X, Y
         A.check()
         formats = {}
@@ -551,7 +582,8 @@ def run_ours(args, world: int, rank: int, local: int):
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-               "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args, world),
+               "vs_baseline": None, "dtype": "f32" if args.acc == "fp32" else "f64", "data": "synthetic",
+               "config": workload_config(args, world),
                "pct_hbm_peak": value / world / peaks["hbm_gbs"], "pct_hbm_8tbs_spec": value / world / 8000.0,
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                "gpu_launches": int(info["launches"]) * args.steps,

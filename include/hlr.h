@@ -115,6 +115,13 @@ typedef struct {
  * whatever the matrix size (it costs 24 bytes of host memory per column slice), e.g. to check
  * the stored codes of a large matrix against an independent decoder. */
 #define HLR_DECODE_MAP (1 << 16)
+/* OR-ed into hlr_hmatrix_desc.tuning (any format): the launch shape of the persistent product
+ * kernels. Their work lists are made for k CTAs per SM (1..8; 0, the default, = as many as the
+ * single-column FP32 kernels keep resident; values above that are treated as that). A kernel
+ * variant that keeps fewer CTAs resident (FP64 accumulation, multi-column passes) runs one
+ * wave of CTAs that each walk several lists, so a matrix used mostly with such a variant is
+ * better balanced with k equal to that variant's residency. The result does not depend on k. */
+#define HLR_CTAS_PER_SM(k) ((k) << 20)
 
 /* Sizes of an uploaded matrix (hlr_get_info). Byte counts exclude alignment padding. */
 typedef struct {
@@ -163,8 +170,11 @@ int hlr_matvec_host(hlr_handle h, const double *x_host, double *y_host, int flag
  * products each (permute, phase 1, combine, phase 2 per launch group; the job list is a kernel
  * parameter, so no device memory is allocated per call and the call can be captured in a CUDA
  * graph once the scratch below exists). With HLR_ACC_FP32, requests with several columns
- * (and every request under HLR_MULTI) run in passes of 8 columns that decode each value once;
- * their pass scratch is allocated per handle on first use (call once before capturing).
+ * (and every request under HLR_MULTI) run in passes of up to 32 columns that decode each value
+ * once (a pass of at most 8 columns takes narrower kernels with the same per-column arithmetic,
+ * so a column's bits do not depend on the pass width); their pass scratch is allocated per
+ * handle on first use and grown when a request needs more passes (call once with the widest
+ * requests before capturing).
  * FP64 accumulation and plain FP64 storage run one product per column.
  * Errors: HLR_ERR_INVALID, HLR_ERR_OOM, HLR_ERR_CUDA. Section 5.4 (applied per column). */
 int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,
@@ -303,7 +313,7 @@ int hlr_decode_units(hlr_handle h, double *out_dev, int64_t cap, void *cuda_stre
  * (each of its seven parts rounded up to 256 bytes); a matrix whose map does not fit is
  * rejected with HLR_ERR_UNSUPPORTED and a message giving the bytes it needs.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
+ * that device current).
  * All calls share the one array and it keeps the last call's map: every call rewrites all of
  * the map it reads before its kernel runs, so nothing has to start at zero, but calls whose
  * copies or kernels overlap on the GPU (different streams or threads without ordering between

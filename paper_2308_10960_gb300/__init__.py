@@ -190,14 +190,17 @@ class DeviceHMatrix:
             pass
 
 
-def tuning_code(sub_rows: int = 64, leaf_rows: int = 64, piece_kb: int = 16) -> int:
-    """HLR_TUNING of include/hlr.h: rows per lane of an X column (32/64/128), rows of a
-    phase-2 task (32/64), piece size in KiB (4..16); the defaults give 0."""
-    if (sub_rows, leaf_rows, piece_kb) == (64, 64, 16):
-        return 0
-    if sub_rows not in (32, 64, 128) or leaf_rows not in (32, 64) or not 4 <= piece_kb <= 16:
+def tuning_code(sub_rows: int = 64, leaf_rows: int = 64, piece_kb: int = 16, ctas_per_sm: int = 0) -> int:
+    """HLR_TUNING | HLR_CTAS_PER_SM of include/hlr.h: rows per lane of an X column (32/64/128),
+    rows of a phase-2 task (32/64), piece size in KiB (4..16), CTAs per SM the work lists are
+    made for (0 = as many as are resident, 1..8); the defaults give 0."""
+    if sub_rows not in (32, 64, 128) or leaf_rows not in (32, 64) or not 4 <= piece_kb <= 16 \
+            or not 0 <= ctas_per_sm <= 8:
         raise HlrError(HLR_ERR_INVALID, "bad tuning")
-    return (sub_rows.bit_length() - 1) | ((leaf_rows.bit_length() - 1) << 4) | (piece_kb << 8)
+    shape = int(ctas_per_sm) << 20
+    if (sub_rows, leaf_rows, piece_kb) == (64, 64, 16):
+        return shape
+    return (sub_rows.bit_length() - 1) | ((leaf_rows.bit_length() - 1) << 4) | (piece_kb << 8) | shape
 
 
 def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None, tuning: int = 0) -> DeviceHMatrix:

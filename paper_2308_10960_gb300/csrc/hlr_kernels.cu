@@ -65,11 +65,12 @@ template <>
 struct Tr<FMT_DFL32> : Tr<FMT_AFL32> {};
 template <>
 struct Tr<FMT_MP32> : Tr<FMT_AFL32> {};
-constexpr int kRB = 8;          // right-hand sides per pass of the multi-RHS product
+constexpr int kRB = 32;         // right-hand sides per pass of the multi-RHS product (widest pass)
+constexpr int kRN = 8;          // width of the narrow pass, for requests of at most 8 columns
 constexpr int kMaxBatch = 64;   // products per launch of the batched path
 
 // One product of a launch. Single right-hand side (R = 1): y += A~ x with the handle's scratch.
-// Multi-RHS pass (R = kRB): Y(:, 0:nrhs) += A~ X(:, 0:nrhs) for nrhs <= kRB columns, with the
+// Multi-RHS pass (R = kRN or kRB): Y(:, 0:nrhs) += A~ X(:, 0:nrhs) for nrhs <= R columns, with the
 // pass's own scratch (xp, tw, part).
 struct Job {
   DevLayout L;
@@ -77,9 +78,9 @@ struct Job {
   double *y;         // y (R = 1) or the pass's first column of Y (leading dim ldy)
   int64_t ldx, ldy;
   int32_t nrhs, pad;
-  float *xp;         // R = kRB: X in cluster order, kRB floats per row      [n + 8][kRB]
-  float *tw;         // R = kRB: t m_min(W), kRB per lowrank column          [rank_sum + 8][kRB]
-  double *part;      // R = kRB: phase-1 chunk partial sums, kRB per entry   [part_total + 1][kRB]
+  float *xp;         // R > 1: X in cluster order, R floats per row          [n + 8][R]
+  float *tw;         // R > 1: t m_min(W), R per lowrank column              [rank_sum + 8][R]
+  double *part;      // R > 1: phase-1 chunk partial sums, R per entry       [part_total + 1][R]
 };
 // A launch's products, passed by value as a kernel parameter (no device-side descriptor copy,
 // so a batched launch needs no allocation and can be captured in a graph).
@@ -98,21 +99,21 @@ template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t slot_bytes() {
   return size_t(kPieceMax) + kSlotPad + (R == 1 ? size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz : 0);
 }
-// phase-2 transposition tiles of one warp: 16 rows x 33 (single RHS, accumulation type) or
-// kRB x 4 rows x 33 floats (multi-RHS)
+// phase-2 tiles of one warp: 16 rows x 33 (single RHS, accumulation type) or, for a multi-RHS
+// pass, a 16 x 36 decode tile and the 32 slices' R multipliers (floats)
 template <int FMT, int R>
 __host__ __device__ constexpr size_t tile_bytes() {
-  return R > 1 ? (size_t(16) * 36 + 32 * kRB) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
+  return R > 1 ? (size_t(16) * 36 + 32 * R) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
 }
 // dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers (single RHS:
-// two halves; multi-RHS: kRB sums per row and warp, sharing the space of the tiles)
+// two halves; multi-RHS: the tiles, and in the same space, once a leaf is done, each warp's
+// 64 x R row sums at stride R + 8)
 template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
   return size_t(kStages) * slot_bytes<FMT, PH, R>() + 2 * kStages * 8 + 16 +
          (PH == 0 ? 0
-          : R > 1 ? (size_t(kCWarps) * tile_bytes<FMT, R>() > size_t(kCWarps) * 64 * kRB * 8
-                         ? size_t(kCWarps) * tile_bytes<FMT, R>()
-                         : size_t(kCWarps) * 64 * kRB * 8)
+          : R > 1 ? (tile_bytes<FMT, R>() > size_t(64) * (R + 8) * 4 ? size_t(kCWarps) * tile_bytes<FMT, R>()
+                                                                     : size_t(kCWarps) * 64 * (R + 8) * 4)
                   : 2 * kCWarps * 64 * 8 + size_t(kCWarps) * tile_bytes<FMT, R>());
 }
 
@@ -434,19 +435,19 @@ __global__ void k_permute(const __grid_constant__ Jobs<NB> J) {
   }
 }
 
-// X_perm for a multi-RHS pass: row p holds X(perm[p], 0:kRB) in FP32, zero beyond nrhs
-template <int NB>
+// X_perm for a multi-RHS pass: row p holds X(perm[p], 0:R) in FP32, zero beyond nrhs
+template <int R, int NB>
 __global__ void k_permute_multi(const __grid_constant__ Jobs<NB> J) {
   const Job &jb = J.j[blockIdx.y];
   const DevLayout &L = jb.L;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < L.n; p += int64_t(gridDim.x) * blockDim.x) {
     const int64_t g = __ldg(L.perm + p);
-    float v[kRB];
+    float v[R];
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) v[q] = q < jb.nrhs ? float(__ldg(jb.x + q * jb.ldx + g)) : 0.f;
-    float4 *dst = reinterpret_cast<float4 *>(jb.xp + p * kRB);
+    for (int q = 0; q < R; ++q) v[q] = q < jb.nrhs ? float(__ldg(jb.x + q * jb.ldx + g)) : 0.f;
+    float4 *dst = reinterpret_cast<float4 *>(jb.xp + p * R);
 #pragma unroll
-    for (int q = 0; q < kRB / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int q = 0; q < R / 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
   }
 }
 
@@ -788,7 +789,7 @@ __device__ bool consume_phase1_pairs(const DevLayout &L, uint32_t np, uint32_t &
 
 // Columns of blocks whose phase-1 work is split into chunks: sum the partial sums in chunk
 // order and apply the column factor (deterministic, no atomics). One product per blockIdx.y;
-// R = kRB handles the kRB right-hand sides of a multi-RHS pass.
+// R > 1 handles the R right-hand sides of a multi-RHS pass.
 template <int FMT, int R, int NB>
 __global__ void k_combine(const __grid_constant__ Jobs<NB> J) {
   const Job &jb = J.j[blockIdx.y];
@@ -805,8 +806,8 @@ __global__ void k_combine(const __grid_constant__ Jobs<NB> J) {
       else
         L.tw64[c.tidx] = sum * L.fac64[c.tidx];
     } else {
-      for (uint32_t k = 0; k < c.nchunks; ++k) sum += jb.part[(size_t(c.pbase) + k) * kRB + q];
-      jb.tw[size_t(c.tidx) * kRB + q] = float(sum * double(L.fac32[c.tidx]));
+      for (uint32_t k = 0; k < c.nchunks; ++k) sum += jb.part[(size_t(c.pbase) + k) * R + q];
+      jb.tw[size_t(c.tidx) * R + q] = float(sum * double(L.fac32[c.tidx]));
     }
   }
 }
@@ -1487,14 +1488,15 @@ __device__ bool consume_phase2_rows(const DevLayout &L, uint32_t np, uint32_t &i
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 1 (FP32): as consume_phase1, but every lane keeps kRB dot products; the
-// x rows come from the pass's X_perm in global memory (kRB floats per row, through L1) and the
+// Multi-RHS pass, phase 1 (FP32): as consume_phase1, but every lane keeps R dot products; the
+// x rows come from the pass's X_perm in global memory (R floats per row, through L1) and the
 // column factors from fac32.
 // ---------------------------------------------------------------------------------------------
+template <int R>
 __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                      uint64_t *empty) {
   const DevLayout &L = jb.L;
-  constexpr size_t slot = slot_bytes<FMT_AFL32, 0, kRB>();
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 0, R>();
   const int t = threadIdx.x, lane = t & 31;
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   for (uint32_t i = 0; i < np; ++i, ++it) {
@@ -1507,9 +1509,9 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
     const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
     const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
     const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
-    float acc[kRB];
+    float acc[R];
 #pragma unroll
-    for (int q = 0; q < kRB; ++q) acc[q] = 0.f;
+    for (int q = 0; q < R; ++q) acc[q] = 0.f;
     uint32_t G = 1;
     const Seg *sgp = nullptr;
     int j = 0;
@@ -1524,8 +1526,8 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
         const int sub = t & int(G - 1);
         lead = sub == 0;
         const int rc = (int(sg.nr) - sub + int(G) - 1) >> sg.lg;   // rows sub, sub + G, ...
-        const float4 *xr = xp4 + (size_t(sg.gx) + sub) * (kRB / 4);
-        const int xs = int(G) * (kRB / 4);
+        const float4 *xr = xp4 + (size_t(sg.gx) + sub) * (R / 4);
+        const int xs = int(G) * (R / 4);
         const uint32_t *col = Wd + bc_column(ph, t);
         const ColDec c = lane_dec(h);
 #pragma unroll 4
@@ -1538,7 +1540,7 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
           else
             v = float(dec_f64(bc_code64(col, uint32_t(r) * c.w), c));
 #pragma unroll
-          for (int hh = 0; hh < kRB / 4; ++hh) {
+          for (int hh = 0; hh < R / 4; ++hh) {
             const float4 xv = __ldg(xr + r * xs + hh);
             acc[4 * hh] = fmaf(v, xv.x, acc[4 * hh]);
             acc[4 * hh + 1] = fmaf(v, xv.y, acc[4 * hh + 1]);
@@ -1552,7 +1554,7 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
 #pragma unroll
     for (uint32_t o = 1; o < 32; o <<= 1) {
 #pragma unroll
-      for (int q = 0; q < kRB; ++q) {
+      for (int q = 0; q < R; ++q) {
         const float v = __shfl_xor_sync(kFull, acc[q], o);
         if (o < G) acc[q] += v;
       }
@@ -1561,14 +1563,14 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
       const Seg &sg = *sgp;
       if (sg.x.nchunks == 1) {
         const float f = __ldg(L.fac32 + sg.tidx + j);
-        float4 *dst = reinterpret_cast<float4 *>(jb.tw + (size_t(sg.tidx) + j) * kRB);
+        float4 *dst = reinterpret_cast<float4 *>(jb.tw + (size_t(sg.tidx) + j) * R);
 #pragma unroll
-        for (int hh = 0; hh < kRB / 4; ++hh)
+        for (int hh = 0; hh < R / 4; ++hh)
           dst[hh] = make_float4(acc[4 * hh] * f, acc[4 * hh + 1] * f, acc[4 * hh + 2] * f, acc[4 * hh + 3] * f);
       } else {
-        double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * kRB;
+        double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * R;
 #pragma unroll
-        for (int q = 0; q < kRB; ++q) dst[q] = double(acc[q]);
+        for (int q = 0; q < R; ++q) dst[q] = double(acc[q]);
       }
     }
     release_slot(&empty[s]);
@@ -1577,14 +1579,16 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 2 on the tensor cores: per warp and piece, Y|leaf (rows x kRB) +=
-// W~(rows x 32 slices) T(32 slices x kRB) as mma.sync m16n8k8 TF32 products. Every lane decodes
+// Multi-RHS pass, phase 2 on the tensor cores: per warp and piece, Y|leaf (rows x R) +=
+// W~(rows x 32 slices) T(32 slices x R) as mma.sync m16n8k8 TF32 products. Every lane decodes
 // its slice (its bank column) 16 rows at a time into a padded shared-memory tile, from which the
-// A fragments are read; the multipliers of the 32 slices form the B fragments. Each FP32 operand
-// is split into two TF32 parts (hi + lo) and the product is the sum of the four part products,
-// so the contraction keeps FP32 accuracy (the lo*lo term is below 2^-22 relative). The products
-// of a piece are accumulated in FP32 registers (C fragments), added to compensated FP32 pairs
-// across the pieces of the leaf, and summed over the warps in FP64 into Y.
+// A fragments are read; the R multipliers of the 32 slices form the B fragments of the R / 8
+// column tiles. Each FP32 operand is split into two TF32 parts (hi + lo) and a product is the sum
+// of three part products (hi hi, hi lo, lo hi; the lo lo term is below 2^-22 relative), so the
+// contraction keeps FP32 accuracy. A piece's products go into fresh C fragments, which are then
+// added to the leaf's FP32 sums in registers (one add per piece and entry, as the single-RHS row
+// sums take one term per slice); at the end of the leaf the warps' sums are added in FP64, in
+// fixed order, into Y.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t tf32_of(float x) {
   uint32_t r;
@@ -1599,19 +1603,26 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+template <int R>
 __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                          uint64_t *empty, float *tiles) {
   const DevLayout &L = jb.L;
-  constexpr size_t slot = slot_bytes<FMT_AFL32, 1, kRB>();
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 1, R>();
   constexpr int kTS = 36;  // tile row stride (floats): conflict-free stores by lane and fragment loads
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int g = lane >> 2, tq = lane & 3;  // mma fragment coordinates
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
-  float *tile = tiles + warp * (16 * kTS + 32 * kRB);
-  float *mbuf = tile + 16 * kTS;                      // [32 slices][kRB] multipliers of the warp
-  double *red = reinterpret_cast<double *>(tiles);    // used at the end of a leaf, after a barrier
-  Comp32 acc[4][4];  // per 16-row tile: C fragment (rows g, g + 8; columns 2 tq, 2 tq + 1)
+  float *tile = tiles + warp * (16 * kTS + 32 * R);
+  float *mbuf = tile + 16 * kTS;                              // [32 slices][R] multipliers of the warp
+  float *red = tiles;  // [kCWarps][64 rows][R + 8] leaf sums, over the tiles once every warp is done
+  float c[4][R / 8][4];  // per 16-row tile and 8-column tile: C fragment (rows g, g + 8; columns 2 tq, 2 tq + 1)
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < R / 8; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) c[a][b][e] = 0.f;
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -1624,52 +1635,46 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
     const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
     const int nr = ph->nr;
     const uint32_t flags = ph->flags;
+    const uint32_t row0 = ph->row0;
     if (flags & PF_START_LEAF) {
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b].reset();
+        for (int b = 0; b < R / 8; ++b)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) c[a][b][e] = 0.f;
     }
-    // the lane's slice and its kRB multipliers (zero for idle lanes)
-    float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo;
+    // the lane's slice and its R multipliers (zero for idle lanes)
     LaneHdr hd{0xff, 0, 0, 0};
     const uint32_t *col = Wd;
     bool active = false;
+    float4 *mrow = reinterpret_cast<float4 *>(mbuf + lane * R);
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
         const Seg &sg = segs[h.seg];
         if (sg.kind == SEG_DENSE) {
           const float mm = float(sg.m_min);
-          const float4 x0 = __ldg(xp4 + (size_t(sg.gx) + h.j) * (kRB / 4));
-          const float4 x1 = __ldg(xp4 + (size_t(sg.gx) + h.j) * (kRB / 4) + 1);
-          lo = make_float4(x0.x * mm, x0.y * mm, x0.z * mm, x0.w * mm);
-          hi = make_float4(x1.x * mm, x1.y * mm, x1.z * mm, x1.w * mm);
+#pragma unroll
+          for (int q = 0; q < R / 4; ++q) {
+            const float4 xv = __ldg(xp4 + (size_t(sg.gx) + h.j) * (R / 4) + q);
+            mrow[q] = make_float4(xv.x * mm, xv.y * mm, xv.z * mm, xv.w * mm);
+          }
         } else {
-          lo = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4));
-          hi = __ldg(tw4 + (size_t(sg.gx) + h.j) * (kRB / 4) + 1);
+#pragma unroll
+          for (int q = 0; q < R / 4; ++q) mrow[q] = __ldg(tw4 + (size_t(sg.gx) + h.j) * (R / 4) + q);
         }
         hd = h;
         col = Wd + bc_column(ph, t);
         active = true;
       }
     }
-    reinterpret_cast<float4 *>(mbuf)[lane * 2] = lo;
-    reinterpret_cast<float4 *>(mbuf)[lane * 2 + 1] = hi;
-    __syncwarp();
-    // B fragments of the four 8-slice groups: B[k][n] = multiplier n of slice 8 kg + k
-    uint32_t bh[4][2], bl[4][2];
+    if (!active) {
 #pragma unroll
-    for (int kg = 0; kg < 4; ++kg) {
-#pragma unroll
-      for (int h2 = 0; h2 < 2; ++h2) {
-        const float bv = mbuf[(8 * kg + tq + 4 * h2) * kRB + g];
-        bh[kg][h2] = tf32_of(bv);
-        bl[kg][h2] = tf32_of(bv - __uint_as_float(bh[kg][h2]));
-      }
+      for (int q = 0; q < R / 4; ++q) mrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const ColDec c = lane_dec(hd);
-    const bool fast = __all_sync(kFull, !active || c.fast32);
+    const ColDec cd = lane_dec(hd);
+    const bool fast = __all_sync(kFull, !active || cd.fast32);
 #pragma unroll
     for (int mt = 0; mt < 4; ++mt) {  // 16-row tiles of the leaf
       if (16 * mt >= nr) break;
@@ -1678,16 +1683,22 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
       for (int rr = 0; rr < 16; ++rr) {
         const int r = 16 * mt + rr;
         const bool ok = active && r < nr;
-        const uint32_t bit = uint32_t(ok ? r : 0) * c.w;
+        const uint32_t bit = uint32_t(ok ? r : 0) * cd.w;
         float v;
         if (fast)
-          v = dec_f32(bc_code32(col, bit), c);
+          v = dec_f32(bc_code32(col, bit), cd);
         else
-          v = float(dec_any64(bc_code64(col, bit), c, VF_AFL));
+          v = float(dec_any64(bc_code64(col, bit), cd, VF_AFL));
         tile[rr * kTS + lane] = ok ? v : 0.f;
       }
       __syncwarp();
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      // this piece's part of the 16 rows, accumulated apart and then added to the leaf's sums,
+      // so that no FP32 accumulator takes more than one term per piece (as the single-RHS lanes)
+      float d[R / 8][4];
+#pragma unroll
+      for (int nt = 0; nt < R / 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
 #pragma unroll
       for (int kg = 0; kg < 4; ++kg) {
         const float av[4] = {tile[g * kTS + 8 * kg + tq], tile[(g + 8) * kTS + 8 * kg + tq],
@@ -1698,51 +1709,57 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
           ah[q] = tf32_of(av[q]);
           al[q] = tf32_of(av[q] - __uint_as_float(ah[q]));
         }
-        mma_tf32(d, al, bl[kg][0], bl[kg][1]);
-        mma_tf32(d, al, bh[kg][0], bh[kg][1]);
-        mma_tf32(d, ah, bl[kg][0], bl[kg][1]);
-        mma_tf32(d, ah, bh[kg][0], bh[kg][1]);
+#pragma unroll
+        for (int nt = 0; nt < R / 8; ++nt) {
+          // B[k][n] = multiplier n of slice 8 kg + k, columns 8 nt .. 8 nt + 7
+          const float b0 = mbuf[(8 * kg + tq) * R + 8 * nt + g], b1 = mbuf[(8 * kg + tq + 4) * R + 8 * nt + g];
+          const uint32_t bh0 = tf32_of(b0), bh1 = tf32_of(b1);
+          const uint32_t bl0 = tf32_of(b0 - __uint_as_float(bh0)), bl1 = tf32_of(b1 - __uint_as_float(bh1));
+          mma_tf32(d[nt], al, bh0, bh1);
+          mma_tf32(d[nt], ah, bl0, bl1);
+          mma_tf32(d[nt], ah, bh0, bh1);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[mt][q].add(d[q]);
+      for (int nt = 0; nt < R / 8; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[mt][nt][e] += d[nt][e];
       __syncwarp();  // the tile is rewritten for the next rows
     }
+    release_slot(&empty[s]);  // the slot is not read after this point
     if (flags & PF_END_LEAF) {
-      bar_consumers();  // every warp is done with its tile before the sums reuse the space
+      bar_consumers();  // every warp is past its tile reads
+      float *wr = red + warp * (64 * (R + 8));
 #pragma unroll
-      for (int mt = 0; mt < 4; ++mt) {
-        red[(warp * 64 + 16 * mt + g) * kRB + 2 * tq] = acc[mt][0].value();
-        red[(warp * 64 + 16 * mt + g) * kRB + 2 * tq + 1] = acc[mt][1].value();
-        red[(warp * 64 + 16 * mt + g + 8) * kRB + 2 * tq] = acc[mt][2].value();
-        red[(warp * 64 + 16 * mt + g + 8) * kRB + 2 * tq + 1] = acc[mt][3].value();
-      }
+      for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < R / 8; ++nt) {
+          *reinterpret_cast<float2 *>(wr + (16 * mt + g) * (R + 8) + 8 * nt + 2 * tq) = make_float2(c[mt][nt][0], c[mt][nt][1]);
+          *reinterpret_cast<float2 *>(wr + (16 * mt + g + 8) * (R + 8) + 8 * nt + 2 * tq) =
+              make_float2(c[mt][nt][2], c[mt][nt][3]);
+        }
       bar_consumers();
-      const uint32_t row0 = ph->row0;
       for (int idx = t; idx < nr * jb.nrhs; idx += kConsumers) {
         const int row = idx / jb.nrhs, q = idx - row * jb.nrhs;
         double sum = 0.0;
 #pragma unroll
-        for (int w = 0; w < kCWarps; ++w) sum += red[(w * 64 + row) * kRB + q];
+        for (int w = 0; w < kCWarps; ++w) sum += double(red[(w * 64 + row) * (R + 8) + q]);
         double *yp = jb.y + size_t(q) * size_t(jb.ldy) + __ldg(L.perm + row0 + uint32_t(row));
         *yp += sum;  // the only update of this entry (its leaf has one owner CTA)
       }
       bar_consumers();
     }
-    release_slot(&empty[s]);
   }
   return true;
 }
 
-// Persistent product kernel over the products of one launch (J.n <= NB). Every CTA walks its
-// range of each product's piece stream in turn; the ring slots and their mbarrier phases run on
-// across products.
 // resident CTAs per SM the product kernels are compiled for: the FP64-accumulation kernels keep
 // 64 FP64 row sums per thread in phase 2
-template <int FMT>
-constexpr int kMinBlocks = FMT == FMT_AFL64 ? 2 : 4;
+template <int FMT, int R>
+constexpr int kMinBlocks = FMT == FMT_AFL64 ? 2 : R > kRN ? 3 : 4;
 
 template <int FMT, int PH, int R, int NB>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<FMT>) k_product(const __grid_constant__ Jobs<NB> J) {
+__global__ void __launch_bounds__(kThreads, (kMinBlocks<FMT, R>)) k_product(const __grid_constant__ Jobs<NB> J) {
   extern __shared__ __align__(128) uint8_t smem[];
   constexpr size_t slot = slot_bytes<FMT, PH, R>();
   uint64_t *full = reinterpret_cast<uint64_t *>(smem + size_t(kStages) * slot);
@@ -1774,9 +1791,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<FMT>) k_product(const __g
     bool ok;
     if constexpr (R > 1) {
       if constexpr (PH == 0)
-        ok = consume_phase1_multi(jb, np, it, smem, full, empty);
+        ok = consume_phase1_multi<R>(jb, np, it, smem, full, empty);
       else
-        ok = consume_phase2_multi_mma(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
+        ok = consume_phase2_multi_mma<R>(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
     } else if constexpr (PH == 0 && FMT == FMT_AFL32) {
       ok = consume_phase1_pairs(jb.L, np, it, smem, full, empty);
     } else if constexpr (PH == 0 && FMT == FMT_AFL64) {
@@ -1888,6 +1905,8 @@ struct DevProps {
   int sms = 0;
   int occ[2] = {0, 0};    // resident CTAs per SM of the phase-1 / phase-2 kernels (FP32 path)
   int occ64[2] = {0, 0};  // the same for the FP64-accumulation kernels
+  int occN[2] = {0, 0};   // the same for the narrow multi-RHS pass kernels (R = kRN)
+  int occR[2] = {0, 0};   // the same for the wide multi-RHS pass kernels (R = kRB)
 };
 std::mutex g_props_mu;
 DevProps g_props[64];
@@ -1905,6 +1924,8 @@ void set_smem_attrs() {
   set_smem_attr<FMT_AFL64, 1, 1, NB>();
   set_smem_attr<FMT_RAW64, 0, 1, NB>();
   set_smem_attr<FMT_RAW64, 1, 1, NB>();
+  set_smem_attr<FMT_AFL32, 0, kRN, NB>();
+  set_smem_attr<FMT_AFL32, 1, kRN, NB>();
   set_smem_attr<FMT_AFL32, 0, kRB, NB>();
   set_smem_attr<FMT_AFL32, 1, kRB, NB>();
   set_smem_attr<FMT_BFL32, 0, 1, NB>();
@@ -1938,6 +1959,18 @@ const DevProps &props(int dev) {
                                                   smem_bytes<FMT_AFL64, 1>());
     P.occ64[0] = o0 < 1 ? 1 : o0;
     P.occ64[1] = o1 < 1 ? 1 : o1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL32, 0, kRB, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 0, kRB>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL32, 1, kRB, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 1, kRB>());
+    P.occR[0] = o0 < 1 ? 1 : o0;
+    P.occR[1] = o1 < 1 ? 1 : o1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k_product<FMT_AFL32, 0, kRN, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 0, kRN>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_product<FMT_AFL32, 1, kRN, 1>, kThreads,
+                                                  smem_bytes<FMT_AFL32, 1, kRN>());
+    P.occN[0] = o0 < 1 ? 1 : o0;
+    P.occN[1] = o1 < 1 ? 1 : o1;
     if (cur != dev) cudaSetDevice(cur);
   }
   return P;
@@ -1968,21 +2001,22 @@ void launch_jobs(const Jobs<NB> &J, cudaStream_t st, cudaEvent_t *ev, int share 
   // work lists of several slots, so that concurrent work keeps the rest of every SM
   auto cap = [share](int nct) { return share > 0 && share < 8 ? std::max(1, (nct * share + 7) / 8) : nct; };
   int nct0 = cap(J.j[0].L.ph[0].nct), nct1 = cap(J.j[0].L.ph[1].nct);
-  if constexpr (FMT == FMT_AFL64) {
-    // fewer of these are resident than there are work lists (made for the FP32 kernels): one
-    // wave of CTAs, each walking several work lists
+  if constexpr (FMT == FMT_AFL64 || R > 1) {
+    // fewer of these are resident than there are work lists (made for the single-RHS FP32
+    // kernels): one wave of CTAs, each walking several work lists
     int dev = 0;
     cudaGetDevice(&dev);
     const DevProps &P = props(dev);
-    nct0 = std::min(nct0, P.sms * P.occ64[0]);
-    nct1 = std::min(nct1, P.sms * P.occ64[1]);
+    const int *occ = R > kRN ? P.occR : R > 1 ? P.occN : P.occ64;
+    nct0 = std::min(nct0, P.sms * occ[0]);
+    nct1 = std::min(nct1, P.sms * occ[1]);
   }
   const dim3 gp(unsigned(std::min<int64_t>((nmax + 255) / 256, 4096)), unsigned(J.n));
   if (ev) cudaEventRecord(ev[0], st);
   if constexpr (R == 1)
     k_permute<NB><<<gp, 256, 0, st>>>(J);
   else
-    k_permute_multi<NB><<<gp, 256, 0, st>>>(J);
+    k_permute_multi<R, NB><<<gp, 256, 0, st>>>(J);
   if (ev) cudaEventRecord(ev[1], st);
   if (np0 > 0) k_product<FMT, 0, R, NB><<<nct0, kThreads, smem_bytes<FMT, 0, R>(), st>>>(J);
   if (ncnt > 0) {
@@ -2130,7 +2164,10 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   Batcher<FMT_MP32, 1> bmp(st, share);
   Batcher<FMT_AFL64, 1> b64(st, share);
   Batcher<FMT_RAW64, 1> braw(st, share);
-  Batcher<FMT_AFL32, kRB> bm(st, share);  // multi-column passes decode the AFL family only
+  // multi-column passes decode the AFL family only; a pass of at most kRN columns takes the
+  // narrow kernels (a column's arithmetic is the same in both, so are its bits)
+  Batcher<FMT_AFL32, kRN> bmn(st, share);
+  Batcher<FMT_AFL32, kRB> bm(st, share);
   // pass scratch first (growing it frees the old one, which no pending product may still use)
   for (int q = 0; q < nreq; ++q) {
     if (nrhs[q] < multi_from || !fp32 || H[q]->L.raw || H[q]->L.vfmt != VF_AFL) continue;
@@ -2160,7 +2197,10 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
         jb.xp = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(xp) + p * stride);
         jb.tw = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(tw) + p * stride);
         jb.part = reinterpret_cast<double *>(reinterpret_cast<uint8_t *>(part) + p * stride);
-        bm.add(&Hq, p, jb);
+        if (jb.nrhs <= kRN)
+          bmn.add(&Hq, p, jb);
+        else
+          bm.add(&Hq, p, jb);
       }
     } else {
       for (int c = 0; c < r; ++c) {
@@ -2186,6 +2226,7 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
   bmp.flush();
   b64.flush();
   braw.flush();
+  bmn.flush();
   bm.flush();
   return cuda_status("hlr_matvec_batched: launch");
 }

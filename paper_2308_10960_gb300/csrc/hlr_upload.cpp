@@ -84,8 +84,10 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL && d->format != HLR_FMT_MP)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
   int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
-  if ((d->tuning >> 16) & ~1) return set_error(HLR_ERR_INVALID, "hlr_upload: unknown tuning flags");
+  if ((d->tuning >> 16) & ~0xf1) return set_error(HLR_ERR_INVALID, "hlr_upload: unknown tuning flags");
   const bool keep_map = (d->tuning & HLR_DECODE_MAP) != 0;
+  const int ctas_sm = (d->tuning >> 20) & 15;  // HLR_CTAS_PER_SM; 0: as many as are resident
+  if (ctas_sm > 8) return set_error(HLR_ERR_INVALID, "hlr_upload: bad tuning (HLR_CTAS_PER_SM above 8)");
   const int32_t layout = d->tuning & 0xffff;
   if (layout != 0) {
     const int sl = layout & 15, ll = (layout >> 4) & 15, kb = (layout >> 8) & 255;
@@ -265,6 +267,11 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
   cudaGetDevice(&dev);
   int nct[2] = {0, 0};
   if (ctas_per_phase(dev, nct) <= 0) return set_error(HLR_ERR_CUDA, "hlr_upload: cannot query the device");
+  if (ctas_sm > 0) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int p = 0; p < 2; ++p) nct[p] = std::min(nct[p], std::max(1, sms) * ctas_sm);
+  }
   PackOutput po;
   const bool want_map = keep_map || values <= kDecodeMapMaxValues;
   int rc = pack_work(in, nct, want_map, &po);

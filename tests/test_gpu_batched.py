@@ -2,7 +2,7 @@
 
 The reference is the oracle's decoded matrix A~ (assembled densely at n <= 4096, Section 5.4)
 applied to every right-hand side: Y_out = Y_in + A~ X. Multi-RHS requests with FP32
-accumulation run the kRB = 8 column passes (a value decoded once, used for every column);
+accumulation run passes of up to 32 columns (a value decoded once, used for every column);
 single columns, FP64 accumulation and plain FP64 storage run the single-RHS kernels, many
 products per persistent launch. Also checked: a request gives the same bits alone and mixed
 with others, the same handle may appear twice, and a batch replays from a captured CUDA graph.
@@ -65,7 +65,7 @@ def _batched(mats, Xs, Y0s, acc="fp32"):
     return [Y.cpu().numpy() for Y in Yd]
 
 
-@pytest.mark.parametrize("r", [2, 8, 13, 32])
+@pytest.mark.parametrize("r", [2, 8, 13, 32, 45])
 @pytest.mark.parametrize("case", ["exp2d", "matern"])
 def test_multi_rhs_matches_oracle(case, r, dense_refs, uploaded):
     H, C, Ad = dense_refs[case]
@@ -148,3 +148,29 @@ def test_batched_validation(uploaded):
     Y = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     with pytest.raises(hg.HlrError):
         hg.matvec_batched([A], [X], [Y])
+
+
+def test_multi_column_bits_do_not_depend_on_pass_width(dense_refs, uploaded):
+    """Under HLR_MULTI a column gets the same bits alone (narrow 8-column pass), inside a
+    13-column request (one wide pass) and inside a 40-column request (a wide and a narrow
+    pass), in the same batched call or in separate ones."""
+    H, C, Ad = dense_refs["matern"]
+    A = uploaded["matern"]
+    X, Y0 = _rhs(H.n, 40, 77)
+
+    def run(mats, Xs, Ys):
+        Xd = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in Xs]
+        Yd = [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in Ys]
+        hg.matvec_batched(mats, Xd, Yd, acc="fp32", multi=True)
+        A.check()
+        torch.cuda.synchronize()
+        return [v.cpu().numpy() for v in Yd]
+
+    wide = run([A], [X], [Y0])[0]
+    _check(Ad, X, Y0, wide, "fp32")
+    for j in (0, 5, 12, 33, 39):
+        alone = run([A], [X[j:j + 1]], [Y0[j:j + 1]])[0]
+        assert np.array_equal(alone.view(np.int64), wide[j:j + 1].view(np.int64)), j
+    mid = run([A, A], [X[:13], X[33:]], [Y0[:13], Y0[33:]])
+    assert np.array_equal(mid[0].view(np.int64), wide[:13].view(np.int64))
+    assert np.array_equal(mid[1].view(np.int64), wide[33:].view(np.int64))

@@ -1,6 +1,6 @@
-"""Work-layout tunings of the AFL kernels (rows per lane, task rows, piece size) give the same
-decoded values bit for bit and products within the FP32 tolerance of the oracle; the autotuner
-picks one of its candidates."""
+"""Work-layout tunings of the AFL kernels (rows per lane, task rows, piece size, CTAs per SM)
+give the same decoded values bit for bit and products within the FP32 tolerance of the oracle;
+the autotuner picks one of its candidates."""
 import numpy as np
 import pytest
 
@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 hg = pytest.importorskip("paper_2308_10960_gb300")
 from paper_2308_10960_gb300 import tune  # noqa: E402
 
-LAYOUTS = [(32, 64, 16), (128, 64, 16), (64, 32, 16), (32, 32, 4), (128, 32, 8)]
+LAYOUTS = [(32, 64, 16), (128, 64, 16), (64, 32, 16), (32, 32, 4), (128, 32, 8), (64, 64, 16, 2), (32, 64, 16, 3)]
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
@@ -34,6 +34,16 @@ def test_tuned_layouts_match_oracle(layout, matern_small_case):
             A.check()
             got = yd.cpu().numpy()
             assert np.linalg.norm(got - yref) / np.linalg.norm(yref) <= tol, (layout, acc)
+        if len(layout) == 4:
+            # a launch shape with fewer CTAs per SM: the multi-column passes too (one wide pass)
+            X = np.random.default_rng(5).standard_normal((12, p.n))
+            Y = torch.zeros((12, p.n), dtype=torch.float64, device="cuda")
+            hg.matvec_batched([A], [torch.from_numpy(X).cuda()], [Y], acc="fp32")
+            A.check()
+            got = Y.cpu().numpy()
+            for j in (0, 7, 11):
+                yj = omv.matvec(C, X[j])
+                assert np.linalg.norm(got[j] - yj) / np.linalg.norm(yj) <= 1e-6, (layout, j)
     finally:
         A.free()
 
