@@ -370,8 +370,11 @@ def serve_leg(dev, eps: float) -> dict:
         plan.append((i, "solve" if g.random() < 0.3 else "matvec", m, arr[i]))
     xs = {i: torch.from_numpy(synth.rhs(host[m].n, 7000 + i)).to(dev) for i, _, m, _ in plan}
 
+    ys = {i: torch.zeros_like(x) for i, x in xs.items()}    # the clients' output buffers
+
     def requests(kinds):
-        return [serve.Request(i, k, m, xs[i], arrival=a, rtol=1e-8, maxit=50000) for i, k, m, a in plan if k in kinds]
+        return [serve.Request(i, k, m, xs[i], arrival=a, rtol=1e-8, maxit=50000, y=ys[i])
+                for i, k, m, a in plan if k in kinds]
     # the same product requests at the same arrival times with no solves running: the latency
     # a product has alone, against which the mixed run's product latency is read
     torch.cuda.synchronize()
@@ -541,6 +544,16 @@ def run_ours(args, world: int, rank: int, local: int):
                   "rejected_units": rejected, "vs_build_time": te / t_build}
         del v_d, o_d, u_d
         torch.cuda.empty_cache()
+        # the whole upload (encode, re-place, copy) with the host encoder and with compression on
+        # the GPU during the upload (HLR_ENCODE_DEVICE): wall clock, same matrix bytes
+        for how, dev_enc in (("host_encode", False), ("device_encode", True)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Au = Hh.upload("afl", encode_device=dev_enc)
+            torch.cuda.synchronize()
+            encode[f"upload_s_{how}"] = time.perf_counter() - t0
+            assert Au.info["stream_bytes"] == info["stream_bytes"]
+            Au.free()
         extra.update({
             "encode_device": encode,
             "formats": formats,
@@ -614,12 +627,22 @@ def run_batch(args, world: int, rank: int, local: int):
     dev = torch.device("cuda", local)
     sizes = synth.batch_sizes(48)
     nrhs = synth.batch_nrhs(48)
+    from paper_2308_10960_gb300 import tune
     t0 = time.perf_counter()
+    tuner = tune.Autotuner(reps=10)
+    tuned, t_tune = {}, 0.0
     mats, Xs, Ys, bytes_step, rhs_single = [], [], [], 0.0, 0.0
     for i, (n, r) in enumerate(zip(sizes, nrhs)):
         p = synth.matern_problem(n, seed=100 + i)
         Hh = hg.build_kernel_hmatrix(p.points, "matern15", args.eps, scale=p.params["scale"], diag=p.params["diag"])
-        A = Hh.upload("afl")
+        tt = time.perf_counter()
+        code, rc, res = tuner.choose(Hh, r)      # work layout and launch shape per rank class
+        t_tune += time.perf_counter() - tt
+        if res is not None:
+            tuned[f"rank~{rc[0]} x{rc[1]} cols"] = {"choice (sub, leaf, piece KiB, CTAs/SM)": list(res.best),
+                                                    "tuned_on_n": n,
+                                                    "ms": {",".join(map(str, k)): round(v, 4) for k, v in res.ms.items()}}
+        A = Hh.upload("afl", tuning=code)
         Hh.free()
         mats.append(A)
         Xs.append(torch.from_numpy(synth.rhs(n * r, 1000 + i)).to(dev).view(r, n) if r > 1
@@ -656,12 +679,15 @@ def run_batch(args, world: int, rank: int, local: int):
     peaks = measured_peaks()
     if rank == 0:
         value = total / el_max / 1e9
-        # kernels per batched call: per class (single-RHS FP32, multi-RHS passes) and group of
-        # <= 64 products: permute, phase 1, combine, phase 2
+        # kernels per batched call: per class (single-RHS FP32; wide passes of 32 columns;
+        # narrow passes of at most 8) and group of <= 64 products: permute, phase 1, combine,
+        # phase 2, and for the single-RHS class the scatter of the row totals (a group never
+        # holds one handle's pass twice, which the 48 distinct matrices never ask for)
         n_single = sum(1 for r in nrhs if r == 1)
-        n_pass = sum((r + 7) // 8 for r in nrhs if r > 1)
-        groups = (n_single + 63) // 64 + (n_pass + 63) // 64
-        launches = 4 * groups
+        n_wide = sum(r // 32 + (1 if r % 32 > 8 else 0) for r in nrhs if r > 1)
+        n_narrow = sum(1 for r in nrhs if r > 1 and 0 < r % 32 <= 8)
+        n_pass = n_wide + n_narrow
+        launches = 5 * ((n_single + 63) // 64) + 4 * ((n_wide + 63) // 64 + (n_narrow + 63) // 64)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": el_max / args.steps * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -671,6 +697,7 @@ def run_batch(args, world: int, rank: int, local: int):
                           "l2": "inputs larger than L2", "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "pct_hbm_peak": value / world / peaks["hbm_gbs"],
                "eager_ms_per_step": eager_el / args.steps * 1e3,
+               "autotuned": tuned, "tune_s": t_tune,
                "algorithmic_bytes_per_step": bytes_step, "build_s": t_build, "clocks": clk,
                "gpu_launches": launches * args.steps}
         print(json.dumps(out), flush=True)
@@ -701,8 +728,21 @@ def run_serve(args, world: int, rank: int, local: int):
         p = synth.matern_problem(n, seed=200 + i)
         host[f"m{i}"] = hg.build_kernel_hmatrix(p.points, "matern15", args.eps, scale=p.params["scale"],
                                                 diag=p.params["diag"])
-    be = serve.GpuBackend(host)
     t_build = time.perf_counter() - t0
+    # work layout and launch shape per rank class, timed as the server runs products (single
+    # columns through the pass kernels)
+    from paper_2308_10960_gb300 import tune
+    tuner = tune.Autotuner(reps=10, multi=True)
+    tunings, tuned = {}, {}
+    tt = time.perf_counter()
+    for name in sorted(host, key=lambda m: int(m[1:])):
+        code, rc, res = tuner.choose(host[name], 1)
+        tunings[name] = code
+        if res is not None:
+            tuned[f"rank~{rc[0]}"] = {"choice (sub, leaf, piece KiB, CTAs/SM)": list(res.best), "tuned_on": name,
+                                      "ms": {",".join(map(str, k)): round(v, 4) for k, v in res.ms.items()}}
+    t_tune = time.perf_counter() - tt
+    be = serve.GpuBackend(host, tunings=tunings)
     budget = int(args.serve_budget_gb * 1e9)
     names = sorted(host, key=lambda m: int(m[1:]))
     rates = [float(r) for r in args.serve_rates.split(",")]
@@ -718,7 +758,7 @@ def run_serve(args, world: int, rank: int, local: int):
             m = names[int(g.integers(len(names)))]
             kind = "solve" if g.random() < args.serve_solve_frac else "matvec"
             x = torch.from_numpy(synth.rhs(host[m].n, 7000 + 100 * ri + i)).to(dev)
-            reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000))
+            reqs.append(serve.Request(i, kind, m, x, arrival=arr[i], rtol=1e-8, maxit=50000, y=torch.zeros_like(x)))
         torch.cuda.synchronize()
         srv = serve.Server(be, budget_bytes=budget, cg_workers=4, max_rhs=32)
         srv.preload(names)           # the matrices are resident before the requests arrive
@@ -752,7 +792,7 @@ def run_serve(args, world: int, rank: int, local: int):
                           "sizes": sizes, "rates": rates, "requests_per_rate": args.serve_requests,
                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                "p99_solve_ms": solve_p99, "per_rate": per_rate, "pct_hbm_peak": last["GB/s"] / peaks["hbm_gbs"],
-               "build_s": t_build, "clocks": clk,
+               "build_s": t_build, "clocks": clk, "autotuned": tuned, "tune_s": t_tune,
                "resident_bytes": {m: be.device_bytes(m) for m in names}}
         print(json.dumps(out), flush=True)
     be.close()

@@ -60,10 +60,12 @@ extern "C" {
 #define HLR_ACC_FP32 1  /* decode to FP32, FP32 sums inside a block, FP64 across blocks into y */
 #define HLR_PROFILE  0x100 /* OR-ed into flags: record CUDA events around each kernel launch of the
                               product on cuda_stream, for hlr_profile_read (adds no synchronisation) */
-#define HLR_MULTI    0x200 /* OR-ed into hlr_matvec_batched flags with HLR_ACC_FP32: run every
-                              request, single columns included, through the multi-right-hand-side
-                              kernels, whose result for a column does not depend on the other
-                              columns or requests it is launched with */
+#define HLR_MULTI    0x200 /* OR-ed into hlr_matvec_batched flags: run every column of every
+                              request as a product of its own (the kernels of hlr_matvec, many per
+                              launch), each on a scratch set of its own, so that a column's result
+                              is bit for bit that of hlr_matvec for it, whatever it is launched
+                              with, and the call never shares scratch with hlr_matvec or
+                              hlr_solve_cg running on the same matrix on another stream */
 
 /* OR-ed into the flags of hlr_matvec, hlr_matvec_host, hlr_matvec_batched and hlr_solve_cg:
  * the persistent product kernels take about eighths/8 of their CTA slots (1..7; 0 or 8 = all),
@@ -122,6 +124,13 @@ typedef struct {
  * wave of CTAs that each walk several lists, so a matrix used mostly with such a variant is
  * better balanced with k equal to that variant's residency. The result does not depend on k. */
 #define HLR_CTAS_PER_SM(k) ((k) << 20)
+/* OR-ed into hlr_hmatrix_desc.tuning (compressed formats): compress the blocks on the GPU as
+ * they are uploaded (Section 5.3: compression where the data is placed, as part of building
+ * the device matrix): the FP64 values go to the device through pinned staging, the unit
+ * parameters and streams come from hlr_encode_device, and the host only re-places the codes.
+ * The result is byte for byte the matrix the host encoder gives. Needs device memory for the
+ * FP64 values and the streams during the call. */
+#define HLR_ENCODE_DEVICE (1 << 17)
 
 /* Sizes of an uploaded matrix (hlr_get_info). Byte counts exclude alignment padding. */
 typedef struct {
@@ -170,11 +179,12 @@ int hlr_matvec_host(hlr_handle h, const double *x_host, double *y_host, int flag
  * products each (permute, phase 1, combine, phase 2 per launch group; the job list is a kernel
  * parameter, so no device memory is allocated per call and the call can be captured in a CUDA
  * graph once the scratch below exists). With HLR_ACC_FP32, requests with several columns
- * (and every request under HLR_MULTI) run in passes of up to 32 columns that decode each value
- * once (a pass of at most 8 columns takes narrower kernels with the same per-column arithmetic,
- * so a column's bits do not depend on the pass width); their pass scratch is allocated per
- * handle on first use and grown when a request needs more passes (call once with the widest
- * requests before capturing).
+ * run in passes of up to 32 columns that decode each value once (phase 2 on the tensor cores;
+ * phase 1 on the tensor cores for a wide pass, with FP32 fused multiply-adds for a pass of at
+ * most 8 columns); their pass scratch is allocated per handle on first use and grown when a
+ * request needs more passes. HLR_MULTI instead runs every column as its own product (see
+ * there) on per-column scratch sets, allocated one by one on first use and kept until
+ * hlr_free. Call once with the widest requests before capturing.
  * FP64 accumulation and plain FP64 storage run one product per column.
  * Errors: HLR_ERR_INVALID, HLR_ERR_OOM, HLR_ERR_CUDA. Section 5.4 (applied per column). */
 int hlr_matvec_batched(int nreq, const hlr_handle *h, const int32_t *nrhs,

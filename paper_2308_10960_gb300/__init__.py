@@ -15,13 +15,14 @@ import os
 import numpy as np
 
 from . import _binding as B
-from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ERR_INVALID, HLR_ERR_NOCONV, HLR_FMT_AFL_APLR,
-                       HLR_FMT_FP64, HLR_KERNEL_EXP, HLR_KERNEL_LAPLACE, HLR_KERNEL_MATERN15, HLR_LOWRANK, HlrError)
+from ._binding import (HLR_ACC_FP32, HLR_ACC_FP64, HLR_DENSE, HLR_ENCODE_DEVICE, HLR_ERR_INVALID, HLR_ERR_NOCONV,
+                       HLR_FMT_AFL_APLR, HLR_FMT_FP64, HLR_KERNEL_EXP, HLR_KERNEL_LAPLACE, HLR_KERNEL_MATERN15,
+                       HLR_LOWRANK, HlrError)
 
 __all__ = [
     "HlrError", "DeviceHMatrix", "HostHMatrix", "upload", "build_kernel_hmatrix", "afl_encode",
     "afl_decode_device", "matvec_batched", "HLR_ACC_FP32", "HLR_ACC_FP64", "HLR_FMT_AFL_APLR", "HLR_FMT_FP64",
-    "HLR_DENSE", "HLR_LOWRANK", "lib_path", "tuning_code", "encode", "encode_device", "unit_arrays",
+    "HLR_DENSE", "HLR_LOWRANK", "HLR_ENCODE_DEVICE", "lib_path", "tuning_code", "encode", "encode_device", "unit_arrays",
     "load_host_hmatrix",
 ]
 
@@ -217,8 +218,9 @@ def upload(n: int, perm, blocks, eps: float, fmt="afl", stream=None, tuning: int
 def matvec_batched(mats, Xs, Ys, acc="fp32", stream=None, multi=False, sm_share: int = 0):
     """Y_q += A~_q X_q for every request q (X_q, Y_q: n_q x r_q column-major float64 CUDA tensors,
     i.e. tensors of shape (r_q, n_q) in row-major memory, or 1-D of length n_q). multi=True
-    (FP32 only) runs single columns through the multi-RHS kernels too, so that a column's result
-    does not depend on what it is batched with."""
+    (HLR_MULTI) runs every column as a product of its own on its own scratch, so that a column's
+    result is bit for bit that of ``matvec`` for it, whatever it is batched with, and the call
+    may overlap with ``matvec`` / ``solve_cg`` on the same matrix on another stream."""
     q = len(mats)
     hs = (C.c_uint64 * q)(*[m.handle for m in mats])
     nr = (C.c_int32 * q)()
@@ -322,13 +324,15 @@ class HostHMatrix:
         return off, prec
 
     def upload(self, fmt="afl", eps: float | None = None, stream=None, tuning: int = 0,
-               decode_map: bool = False) -> DeviceHMatrix:
+               decode_map: bool = False, encode_device: bool = False) -> DeviceHMatrix:
         """Compress (fmt="afl") or copy (fmt="fp64") and upload to the current GPU. tuning:
         work layout of the AFL kernels (``tuning_code``; 0 = default); decode_map: keep the map
-        of decode_units whatever the size (HLR_DECODE_MAP)."""
+        of decode_units whatever the size (HLR_DECODE_MAP); encode_device: compress on the GPU
+        during the upload (HLR_ENCODE_DEVICE; the same bytes as the host encoder)."""
         self.desc.format = _FMT[fmt]
         self.desc.eps = self.eps if eps is None else float(eps)
-        self.desc.tuning = int(tuning) | (B.HLR_DECODE_MAP if decode_map else 0)
+        self.desc.tuning = (int(tuning) | (B.HLR_DECODE_MAP if decode_map else 0)
+                            | (B.HLR_ENCODE_DEVICE if encode_device else 0))
         h = C.c_uint64(0)
         nbytes = C.c_size_t(0)
         B.check(B.lib.hlr_upload(C.byref(self.desc), _stream_ptr(stream), C.byref(h), C.byref(nbytes)))

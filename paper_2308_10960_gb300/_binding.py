@@ -35,6 +35,7 @@ HLR_ACC_FP32 = 1
 HLR_PROFILE = 0x100
 HLR_MULTI = 0x200
 HLR_DECODE_MAP = 1 << 16
+HLR_ENCODE_DEVICE = 1 << 17
 HLR_KERNEL_EXP = 1
 HLR_KERNEL_LAPLACE = 2
 HLR_KERNEL_MATERN15 = 3

@@ -191,6 +191,8 @@ struct Handle {
   void *cg_ws = nullptr;             // CG work vectors (allocated on first solve)
   void *multi_ws = nullptr;          // multi-RHS pass scratch (allocated on first use)
   int multi_passes = 0;              // passes multi_ws holds
+  std::vector<void *> col_ws;        // HLR_MULTI: one single-RHS scratch set per column of a
+                                     // batched call (allocated on first use, never freed early)
   int64_t part_total = 0;            // phase-1 chunk partial sums of one product
   std::vector<void *> prof_ev;       // cudaEvent_t ring: 4 per profiled product
   int prof_n = 0;

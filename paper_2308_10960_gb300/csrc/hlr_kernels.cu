@@ -67,6 +67,10 @@ template <>
 struct Tr<FMT_MP32> : Tr<FMT_AFL32> {};
 constexpr int kRB = 32;         // right-hand sides per pass of the multi-RHS product (widest pass)
 constexpr int kRN = 8;          // width of the narrow pass, for requests of at most 8 columns
+// row stride (floats) of a warp's multipliers in a multi-RHS phase 2: a multiple of 8 that is 8
+// modulo 32, so that the B fragment loads (rows tq, columns g) hit 32 different banks
+template <int R>
+constexpr int kMS = R % 32 == 8 ? R : R + 8;
 constexpr int kMaxBatch = 64;   // products per launch of the batched path
 
 // One product of a launch. Single right-hand side (R = 1): y += A~ x with the handle's scratch.
@@ -103,7 +107,7 @@ __host__ __device__ constexpr size_t slot_bytes() {
 // pass, a 16 x 36 decode tile and the 32 slices' R multipliers (floats)
 template <int FMT, int R>
 __host__ __device__ constexpr size_t tile_bytes() {
-  return R > 1 ? (size_t(16) * 36 + 32 * R) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
+  return R > 1 ? (size_t(16) * 36 + 32 * kMS<R>) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
 }
 // dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers (single RHS:
 // two halves; multi-RHS: the tiles, and in the same space, once a leaf is done, each warp's
@@ -111,7 +115,7 @@ __host__ __device__ constexpr size_t tile_bytes() {
 template <int FMT, int PH, int R = 1>
 __host__ __device__ constexpr size_t smem_bytes() {
   return size_t(kStages) * slot_bytes<FMT, PH, R>() + 2 * kStages * 8 + 16 +
-         (PH == 0 ? 0
+         (PH == 0 ? (R > kRN ? size_t(kCWarps) * (32 * 65 + 64) * 4 : 0)
           : R > 1 ? (tile_bytes<FMT, R>() > size_t(64) * (R + 8) * 4 ? size_t(kCWarps) * tile_bytes<FMT, R>()
                                                                      : size_t(kCWarps) * 64 * (R + 8) * 4)
                   : 2 * kCWarps * 64 * 8 + size_t(kCWarps) * tile_bytes<FMT, R>());
@@ -1488,12 +1492,60 @@ __device__ bool consume_phase2_rows(const DevLayout &L, uint32_t np, uint32_t &i
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 1 (FP32): as consume_phase1, but every lane keeps R dot products; the
-// x rows come from the pass's X_perm in global memory (R floats per row, through L1) and the
-// column factors from fac32.
+// Tensor-core helpers of the multi-RHS passes: TF32 parts of an FP32 operand and the warp-level
+// m16n8k8 TF32 product with FP32 accumulation (fragment layouts of the PTX ISA: A row-major
+// a0 = (g, tq), a1 = (g + 8, tq), a2 = (g, tq + 4), a3 = (g + 8, tq + 4); B column-major
+// b0 = (tq, g), b1 = (tq + 4, g); C c0 = (g, 2 tq), c1 = (g, 2 tq + 1), c2 = (g + 8, 2 tq),
+// c3 = (g + 8, 2 tq + 1), with g = lane / 4 and tq = lane % 4). An FP32 operand x is split into
+// hi = tf32(x) and lo = tf32(x - hi); a product is hi hi + hi lo + lo hi (the lo lo term is
+// below 2^-22 relative), so the contraction keeps FP32 accuracy.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tf32_of(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// d = a b (a fresh C fragment of zeros)
+__device__ __forceinline__ void mma_tf32_z(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+// acc += the three part products of one k step, formed in a fresh fragment and added with FP32
+// rounding, so that no tensor-core accumulation chain is longer than three products
+__device__ __forceinline__ void mma3_add(float (&acc)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                         uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  float d[4];
+  mma_tf32_z(d, al, bh0, bh1);
+  mma_tf32(d, ah, bl0, bl1);
+  mma_tf32(d, ah, bh0, bh1);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) acc[e] += d[e];
+}
+
+__device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_of(x);
+  lo = tf32_of(x - __uint_as_float(hi));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Multi-RHS pass of at most 8 columns, phase 1 (FP32): as consume_phase1, but every lane keeps R
+// dot products; the x rows come from the pass's X_perm in global memory (R floats per row,
+// through L1) and the column factors from fac32. (For 32 columns the x rows would cost 128
+// bytes of L1 traffic per value; that pass uses the tensor cores, below.)
 // ---------------------------------------------------------------------------------------------
 template <int R>
-__device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+__device__ bool consume_phase1_multi_fma(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                      uint64_t *empty) {
   const DevLayout &L = jb.L;
   constexpr size_t slot = slot_bytes<FMT_AFL32, 0, R>();
@@ -1579,30 +1631,182 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
 }
 
 // ---------------------------------------------------------------------------------------------
+// Multi-RHS pass, phase 1 on the tensor cores: for every segment (the X columns of one item of a
+// lowrank block) T^T(R x columns) = X_perm^T(R x rows) X~(rows x columns). Every lane decodes its
+// slice (rows sub, sub + G, ... of one column) into a padded shared-memory tile of its warp (64
+// values per lane and round); then, per segment present in the warp, the warp runs the
+// contraction over the segment's rows in steps of 8: the right-hand sides are the M dimension
+// (R / 16 tiles of 16, or one half-filled tile for R = 8), read from X_perm once per step and
+// segment (8 rows x 16 right-hand sides, one 32-byte sector per row), and up to 32 of the
+// segment's columns in the warp are the N dimension (tiles of 8; row rho of column c is in lane
+// c + rho % G at position rho / G of the tile). Every column's G lanes lie in one warp, so a warp
+// completes the dot products of its columns. A column's T (times its factor), or its chunk
+// partial sum, is written from the C fragments.
+// ---------------------------------------------------------------------------------------------
+template <int R>
+__device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
+                                     uint64_t *empty, float *tiles) {
+  const DevLayout &L = jb.L;
+  constexpr size_t slot = slot_bytes<FMT_AFL32, 0, R>();
+  constexpr int kVS = 65;            // values per lane in the tile (64) + 1: conflict-free stores by row
+  constexpr int MT = (R + 15) / 16;  // M tiles of right-hand sides
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  float *tv = tiles + warp * (32 * kVS + 64);                 // [32 lanes][kVS] decoded values
+  int *clane = reinterpret_cast<int *>(tv + 32 * kVS);        // [32] lanes of a segment's columns
+  int *cj = clane + 32;                                       // [32] their column indices j
+  for (uint32_t i = 0; i < np; ++i, ++it) {
+    const uint32_t s = it % kStages;
+    if (!mbar_wait(&full[s], (it / kStages) & 1)) {
+      atomicOr(L.status, 1u);
+      return false;
+    }
+    const uint8_t *sl = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    LaneHdr h{0xff, 0, 0, 0};
+    if (t < int(ph->ncols)) h = lane_hdrs(sl, ph)[t];
+    const bool active = h.seg != 0xff;
+    int sub = 0, rc = 0;
+    const uint32_t *col = Wd;
+    if (active) {
+      const Seg &sg = segs[h.seg];
+      sub = t & ((1 << sg.lg) - 1);
+      rc = (int(sg.nr) - sub + (1 << sg.lg) - 1) >> sg.lg;   // rows sub, sub + G, ...
+      col = Wd + bc_column(ph, t);
+    }
+    const ColDec c = lane_dec(h);
+    // this lane's values at positions [r0, r0 + 64) of its slice into its tile row
+    auto decode_round = [&](int r0) {
+      const int r1 = min(rc, r0 + 64);
+#pragma unroll 4
+      for (int r = r0; r < r1; ++r) {
+        float v;
+        if (c.fast32)
+          v = dec_f32(bc_code32(col, uint32_t(r) * c.w), c);
+        else if (c.narrow)
+          v = float(dec_f64(bc_code32(col, uint32_t(r) * c.w), c));
+        else
+          v = float(dec_f64(bc_code64(col, uint32_t(r) * c.w), c));
+        tv[lane * kVS + (r - r0)] = v;
+      }
+    };
+    decode_round(0);
+    __syncwarp();
+    const int segme = active ? int(h.seg) : -1;
+    const bool lead = active && sub == 0;
+    uint32_t todo = __ballot_sync(kFull, lead);
+    while (todo) {  // warp-uniform: the segments whose columns lead in this warp
+      const int s0 = __shfl_sync(kFull, segme, __ffs(todo) - 1);
+      const bool mine = lead && segme == s0;
+      const uint32_t mask = __ballot_sync(kFull, mine);
+      todo &= ~mask;
+      const Seg &sg = segs[s0];
+      const int lg = sg.lg, gm = (1 << lg) - 1, nr = sg.nr;
+      const int ncol = __popc(mask);
+      const int nnt = (ncol + 7) >> 3;  // N tiles of 8 columns (1..4)
+      if (mine) {
+        const int k = __popc(mask & ((1u << lane) - 1));
+        clane[k] = lane;
+        cj[k] = h.j;
+      }
+      __syncwarp();
+      // this lane's B columns: column g of every N tile (-1: none)
+      int lc[4];
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) lc[nt] = 8 * nt + g < ncol ? clane[8 * nt + g] : -1;
+      float acc[MT][4][4];
+#pragma unroll
+      for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[m][nt][e] = 0.f;
+      const float *xrow = jb.xp + size_t(sg.gx) * R;
+      for (int rb = 0; rb < nr; rb += 64 << lg) {  // rounds of 64 positions per lane
+        if (rb > 0) {  // a later round (slices longer than 64 rows): this segment's lanes decode it
+          __syncwarp();
+          if (segme == s0) decode_round(rb >> lg);
+          __syncwarp();
+        }
+        const int rend = min(nr, rb + (64 << lg));
+        for (int rho = rb; rho < rend; rho += 8) {
+          const int r0 = rho + tq, r1 = rho + tq + 4;
+          const bool ok0 = r0 < nr, ok1 = r1 < nr;
+          // A = X_perm^T: (right-hand side 16 m + g (+ 8), row r0 / r1)
+          uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+          for (int m = 0; m < MT; ++m) {
+            const int q0 = 16 * m + g, q1 = 16 * m + g + 8;
+            const float a0 = ok0 ? __ldg(xrow + size_t(r0) * R + q0) : 0.f;
+            const float a1 = (ok0 && q1 < R) ? __ldg(xrow + size_t(r0) * R + q1) : 0.f;
+            const float a2 = ok1 ? __ldg(xrow + size_t(r1) * R + q0) : 0.f;
+            const float a3 = (ok1 && q1 < R) ? __ldg(xrow + size_t(r1) * R + q1) : 0.f;
+            tf32_split(a0, ah[m][0], al[m][0]);
+            tf32_split(a1, ah[m][1], al[m][1]);
+            tf32_split(a2, ah[m][2], al[m][2]);
+            tf32_split(a3, ah[m][3], al[m][3]);
+          }
+          const int p0 = (r0 - rb) >> lg, p1 = (r1 - rb) >> lg, s0l = r0 & gm, s1l = r1 & gm;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            if (nt >= nnt) break;
+            // B = X~: (row r0 / r1, column 8 nt + g)
+            const float b0 = (ok0 && lc[nt] >= 0) ? tv[(lc[nt] + s0l) * kVS + p0] : 0.f;
+            const float b1 = (ok1 && lc[nt] >= 0) ? tv[(lc[nt] + s1l) * kVS + p1] : 0.f;
+            uint32_t bh0, bl0, bh1, bl1;
+            tf32_split(b0, bh0, bl0);
+            tf32_split(b1, bh1, bl1);
+#pragma unroll
+            for (int m = 0; m < MT; ++m) mma3_add(acc[m][nt], ah[m], al[m], bh0, bh1, bl0, bl1);
+          }
+        }
+      }
+      // C(right-hand side, column): this lane holds right-hand sides 16 m + g (+ 8) of columns
+      // 8 nt + 2 tq and 8 nt + 2 tq + 1
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt) {
+        if (nt >= nnt) break;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int k = 8 * nt + 2 * tq + cc;
+          if (k >= ncol) continue;
+          const int j = cj[k];
+          if (sg.x.nchunks == 1) {
+            const float f = __ldg(L.fac32 + sg.tidx + j);
+            float *dst = jb.tw + (size_t(sg.tidx) + j) * R;
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+              dst[16 * m + g] = acc[m][nt][cc] * f;
+              if (16 * m + g + 8 < R) dst[16 * m + g + 8] = acc[m][nt][2 + cc] * f;
+            }
+          } else {
+            double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * R;
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+              dst[16 * m + g] = double(acc[m][nt][cc]);
+              if (16 * m + g + 8 < R) dst[16 * m + g + 8] = double(acc[m][nt][2 + cc]);
+            }
+          }
+        }
+      }
+      __syncwarp();  // clane / cj are rewritten for the next segment
+    }
+    release_slot(&empty[s]);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Multi-RHS pass, phase 2 on the tensor cores: per warp and piece, Y|leaf (rows x R) +=
 // W~(rows x 32 slices) T(32 slices x R) as mma.sync m16n8k8 TF32 products. Every lane decodes
 // its slice (its bank column) 16 rows at a time into a padded shared-memory tile, from which the
 // A fragments are read; the R multipliers of the 32 slices form the B fragments of the R / 8
-// column tiles. Each FP32 operand is split into two TF32 parts (hi + lo) and a product is the sum
-// of three part products (hi hi, hi lo, lo hi; the lo lo term is below 2^-22 relative), so the
-// contraction keeps FP32 accuracy. A piece's products go into fresh C fragments, which are then
-// added to the leaf's FP32 sums in registers (one add per piece and entry, as the single-RHS row
-// sums take one term per slice); at the end of the leaf the warps' sums are added in FP64, in
-// fixed order, into Y.
+// column tiles (three TF32 part products per step, mma3_add). Each step's products (8 slices) are
+// added with FP32 rounding to the leaf's sums in registers; at the end of the leaf the warps'
+// sums are added in FP64, in fixed order, into Y.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tf32_of(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 template <int R>
 __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                          uint64_t *empty, float *tiles) {
@@ -1613,8 +1817,9 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
   const int g = lane >> 2, tq = lane & 3;  // mma fragment coordinates
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
-  float *tile = tiles + warp * (16 * kTS + 32 * R);
-  float *mbuf = tile + 16 * kTS;                              // [32 slices][R] multipliers of the warp
+  constexpr int MS = kMS<R>;
+  float *tile = tiles + warp * (16 * kTS + 32 * MS);
+  float *mbuf = tile + 16 * kTS;                              // [32 slices][MS] multipliers of the warp
   float *red = tiles;  // [kCWarps][64 rows][R + 8] leaf sums, over the tiles once every warp is done
   float c[4][R / 8][4];  // per 16-row tile and 8-column tile: C fragment (rows g, g + 8; columns 2 tq, 2 tq + 1)
 #pragma unroll
@@ -1648,7 +1853,7 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
     LaneHdr hd{0xff, 0, 0, 0};
     const uint32_t *col = Wd;
     bool active = false;
-    float4 *mrow = reinterpret_cast<float4 *>(mbuf + lane * R);
+    float4 *mrow = reinterpret_cast<float4 *>(mbuf + lane * MS);
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
@@ -1679,28 +1884,26 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
     for (int mt = 0; mt < 4; ++mt) {  // 16-row tiles of the leaf
       if (16 * mt >= nr) break;
       // this lane's slice, rows 16 mt .. + 15 (rows past the leaf and idle lanes give 0)
+      if (fast) {
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr) {
-        const int r = 16 * mt + rr;
-        const bool ok = active && r < nr;
-        const uint32_t bit = uint32_t(ok ? r : 0) * cd.w;
-        float v;
-        if (fast)
-          v = dec_f32(bc_code32(col, bit), cd);
-        else
-          v = float(dec_any64(bc_code64(col, bit), cd, VF_AFL));
-        tile[rr * kTS + lane] = ok ? v : 0.f;
+        for (int rr = 0; rr < 16; ++rr) {
+          const int r = 16 * mt + rr;
+          const bool ok = active && r < nr;
+          const float v = dec_f32(bc_code32(col, uint32_t(ok ? r : 0) * cd.w), cd);
+          tile[rr * kTS + lane] = ok ? v : 0.f;
+        }
+      } else {  // codes wider than the FP32 fast path: rare, kept out of line of the unrolled loop
+#pragma unroll 1
+        for (int rr = 0; rr < 16; ++rr) {
+          const int r = 16 * mt + rr;
+          const bool ok = active && r < nr;
+          const float v = float(dec_any64(bc_code64(col, uint32_t(ok ? r : 0) * cd.w), cd, VF_AFL));
+          tile[rr * kTS + lane] = ok ? v : 0.f;
+        }
       }
       __syncwarp();
-      // this piece's part of the 16 rows, accumulated apart and then added to the leaf's sums,
-      // so that no FP32 accumulator takes more than one term per piece (as the single-RHS lanes)
-      float d[R / 8][4];
-#pragma unroll
-      for (int nt = 0; nt < R / 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) d[nt][e] = 0.f;
-#pragma unroll
-      for (int kg = 0; kg < 4; ++kg) {
+#pragma unroll 1
+      for (int kg = 0; kg < 4; ++kg) {  // slices 8 kg .. 8 kg + 7 (a loop, to keep the code small)
         const float av[4] = {tile[g * kTS + 8 * kg + tq], tile[(g + 8) * kTS + 8 * kg + tq],
                              tile[g * kTS + 8 * kg + tq + 4], tile[(g + 8) * kTS + 8 * kg + tq + 4]};
         uint32_t ah[4], al[4];
@@ -1712,18 +1915,12 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
 #pragma unroll
         for (int nt = 0; nt < R / 8; ++nt) {
           // B[k][n] = multiplier n of slice 8 kg + k, columns 8 nt .. 8 nt + 7
-          const float b0 = mbuf[(8 * kg + tq) * R + 8 * nt + g], b1 = mbuf[(8 * kg + tq + 4) * R + 8 * nt + g];
+          const float b0 = mbuf[(8 * kg + tq) * MS + 8 * nt + g], b1 = mbuf[(8 * kg + tq + 4) * MS + 8 * nt + g];
           const uint32_t bh0 = tf32_of(b0), bh1 = tf32_of(b1);
           const uint32_t bl0 = tf32_of(b0 - __uint_as_float(bh0)), bl1 = tf32_of(b1 - __uint_as_float(bh1));
-          mma_tf32(d[nt], al, bh0, bh1);
-          mma_tf32(d[nt], ah, bl0, bl1);
-          mma_tf32(d[nt], ah, bh0, bh1);
+          mma3_add(c[mt][nt], ah, al, bh0, bh1, bl0, bl1);
         }
       }
-#pragma unroll
-      for (int nt = 0; nt < R / 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) c[mt][nt][e] += d[nt][e];
       __syncwarp();  // the tile is rewritten for the next rows
     }
     release_slot(&empty[s]);  // the slot is not read after this point
@@ -1791,7 +1988,10 @@ __global__ void __launch_bounds__(kThreads, (kMinBlocks<FMT, R>)) k_product(cons
     bool ok;
     if constexpr (R > 1) {
       if constexpr (PH == 0)
-        ok = consume_phase1_multi<R>(jb, np, it, smem, full, empty);
+        if constexpr (R > kRN)
+          ok = consume_phase1_multi<R>(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
+        else
+          ok = consume_phase1_multi_fma<R>(jb, np, it, smem, full, empty);
       else
         ok = consume_phase2_multi_mma<R>(jb, np, it, smem, full, empty, reinterpret_cast<float *>(red));
     } else if constexpr (PH == 0 && FMT == FMT_AFL32) {
@@ -2119,6 +2319,45 @@ static int multi_scratch(Handle &H, int passes, float **xp, float **tw, double *
   return HLR_OK;
 }
 
+// Single-RHS scratch sets of HLR_MULTI columns: set k of a handle holds what the arena's scratch
+// holds for hlr_matvec (x_perm FP64/FP32, t m_min(W) FP64/FP32, chunk partial sums, row totals),
+// so that columns of one call, and concurrent hlr_matvec / hlr_solve_cg calls on the handle, never
+// share scratch. Sets are allocated one by one when a call needs more and are kept until
+// hlr_free (no cudaFree, which would wait for the whole device, while the handle is in use).
+static int column_scratch(Handle &H, int sets) {
+  const size_t n = size_t(H.L.n), rs = size_t(H.info.rank_sum);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t bytes = al(8 * (n + 8)) + al(4 * (n + 8)) + al(8 * (rs + 8)) + al(4 * (rs + 8)) +
+                       al(8 * size_t(H.part_total) + 8) + al(8 * (n + 8));
+  while (int(H.col_ws.size()) < sets) {
+    void *w = nullptr;
+    if (cudaMalloc(&w, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(HLR_ERR_OOM, "hlr_matvec_batched: column scratch allocation failed");
+    }
+    H.col_ws.push_back(w);
+  }
+  return HLR_OK;
+}
+static DevLayout column_layout(const Handle &H, int k) {
+  const size_t n = size_t(H.L.n), rs = size_t(H.info.rank_sum);
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  uint8_t *b = static_cast<uint8_t *>(H.col_ws[size_t(k)]);
+  DevLayout L = H.L;
+  L.xperm64 = reinterpret_cast<double *>(b);
+  b += al(8 * (n + 8));
+  L.xperm32 = reinterpret_cast<float *>(b);
+  b += al(4 * (n + 8));
+  L.tw64 = reinterpret_cast<double *>(b);
+  b += al(8 * (rs + 8));
+  L.tw32 = reinterpret_cast<float *>(b);
+  b += al(4 * (rs + 8));
+  L.partial = reinterpret_cast<double *>(b);
+  b += al(8 * size_t(H.part_total) + 8);
+  L.ysum = reinterpret_cast<double *>(b);
+  return L;
+}
+
 namespace {
 // Accumulates the products of one kernel class and launches them in groups of <= kMaxBatch.
 // Two products of one group must not share scratch: the same handle appears at most once among
@@ -2156,7 +2395,8 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
     if (H[q]->device != dev) return set_error(HLR_ERR_INVALID, "hlr_matvec_batched: handles of different devices");
   props(dev);
   const bool fp32 = (flags & 0xff) == HLR_ACC_FP32;
-  const int multi_from = (flags & HLR_MULTI) ? 1 : 2;  // fewest columns that take the multi-RHS kernels
+  const bool percol = (flags & HLR_MULTI) != 0;  // every column a single-RHS product of its own
+  const int multi_from = percol ? (1 << 30) : 2;  // fewest columns that take the multi-RHS passes
   const int share = (flags >> 16) & 15;
   Batcher<FMT_AFL32, 1> b32(st, share);
   Batcher<FMT_BFL32, 1> bbfl(st, share);
@@ -2179,10 +2419,52 @@ int launch_batch(int nreq, Handle *const *H, const int32_t *nrhs, const double *
     size_t stride;
     if (int rc = multi_scratch(*H[q], passes, &xp, &tw, &part, &stride)) return rc;
   }
+  // HLR_MULTI: column scratch sets, numbered per handle over the whole call
+  std::vector<std::pair<const Handle *, int>> colbase;  // handle -> sets taken so far
+  if (percol)
+    for (int q = 0; q < nreq; ++q) {
+      if (nrhs[q] <= 0) continue;
+      int need = 0;
+      for (int k = 0; k < nreq; ++k)
+        if (H[k] == H[q] && nrhs[k] > 0) need += nrhs[k];
+      if (int rc = column_scratch(*H[q], need)) return rc;
+    }
+  auto take_sets = [&](const Handle *h, int cnt) {
+    for (auto &cb : colbase)
+      if (cb.first == h) {
+        const int k = cb.second;
+        cb.second += cnt;
+        return k;
+      }
+    colbase.push_back({h, cnt});
+    return 0;
+  };
   for (int q = 0; q < nreq; ++q) {
     Handle &Hq = *H[q];
     const int r = nrhs[q];
     if (r <= 0) continue;
+    if (percol) {
+      // one product per column, each on its own scratch set: the kernels and arithmetic of
+      // hlr_matvec, so a column's bits are those of hlr_matvec of that column
+      const int k0 = take_sets(&Hq, r);
+      for (int c = 0; c < r; ++c) {
+        Job jb = single_job(Hq, X[q] + size_t(c) * size_t(ldx[q]), Y[q] + size_t(c) * size_t(ldy[q]));
+        jb.L = column_layout(Hq, k0 + c);
+        if (Hq.L.raw)
+          braw.add(&Hq, k0 + c, jb);
+        else if (!fp32)
+          b64.add(&Hq, k0 + c, jb);
+        else if (Hq.L.vfmt == VF_BFL)
+          bbfl.add(&Hq, k0 + c, jb);
+        else if (Hq.L.vfmt == VF_DFL)
+          bdfl.add(&Hq, k0 + c, jb);
+        else if (Hq.L.vfmt == VF_MP)
+          bmp.add(&Hq, k0 + c, jb);
+        else
+          b32.add(&Hq, k0 + c, jb);
+      }
+      continue;
+    }
     if (r >= multi_from && fp32 && !Hq.L.raw && Hq.L.vfmt == VF_AFL) {
       const int passes = (r + kRB - 1) / kRB;
       float *xp, *tw;

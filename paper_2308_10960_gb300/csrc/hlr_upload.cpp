@@ -66,6 +66,117 @@ struct HostBuf {
 // Values up to which hlr_decode_units is available (its map costs 24 bytes per slice).
 constexpr int64_t kDecodeMapMaxValues = int64_t(1) << 26;
 
+// HLR_ENCODE_DEVICE: the units' parameters and canonical streams from the GPU encoder
+// (hlr_encode_device) instead of the host's. The values go to the device through two pinned
+// staging buffers (gathered by the host threads, copied while the next chunk is gathered); the
+// parameters and streams come back into prm and a host buffer laid out as the host encoder
+// lays it out (unit u at uoff[u], each stream padded to 16 bytes).
+int encode_units_on_device(int fmt, const std::vector<const double *> &usrc, const std::vector<int64_t> &len,
+                           const std::vector<double> &uprec, cudaStream_t st, std::vector<AflParams> *prm,
+                           std::vector<uint64_t> *uoff, HostBuf *canon) {
+  const int64_t nu = int64_t(usrc.size());
+  std::vector<int64_t> voff(nu + 1, 0);
+  for (int64_t u = 0; u < nu; ++u) voff[u + 1] = voff[u] + len[u];
+  const int64_t total = voff[nu];
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t cap = 8 * size_t(total) + 16 * size_t(nu) + 64;
+  const size_t b_a = al(8 * size_t(total) + 8), b_off = al(8 * size_t(nu + 1)), b_u = al(8 * size_t(nu)),
+               b_mm = al(8 * size_t(nu)), b_e = al(4 * size_t(nu)), b_m = al(4 * size_t(nu)),
+               b_oo = al(8 * size_t(nu + 1)), b_out = al(cap);
+  uint8_t *d = nullptr;
+  if (cudaMalloc(&d, b_a + b_off + b_u + b_mm + b_e + b_m + b_oo + b_out) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(HLR_ERR_OOM, "hlr_upload: device encoding buffers");
+  }
+  struct DevFree {
+    uint8_t *p;
+    ~DevFree() { cudaFree(p); }
+  } dfree{d};
+  double *a_dev = reinterpret_cast<double *>(d);
+  int64_t *off_dev = reinterpret_cast<int64_t *>(d + b_a);
+  double *u_dev = reinterpret_cast<double *>(d + b_a + b_off);
+  double *mm_dev = reinterpret_cast<double *>(d + b_a + b_off + b_u);
+  int32_t *e_dev = reinterpret_cast<int32_t *>(d + b_a + b_off + b_u + b_mm);
+  int32_t *m_dev = reinterpret_cast<int32_t *>(d + b_a + b_off + b_u + b_mm + b_e);
+  int64_t *oo_dev = reinterpret_cast<int64_t *>(d + b_a + b_off + b_u + b_mm + b_e + b_m);
+  uint8_t *out_dev = d + b_a + b_off + b_u + b_mm + b_e + b_m + b_oo;
+  // values, in chunks of kChunk doubles through two pinned buffers
+  constexpr int64_t kChunk = int64_t(1) << 24;  // 128 MiB
+  double *pin[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  auto release = [&]() {
+    for (int k = 0; k < 2; ++k) {
+      if (done[k]) cudaEventSynchronize(done[k]), cudaEventDestroy(done[k]);
+      if (pin[k]) cudaFreeHost(pin[k]);
+    }
+  };
+  for (int k = 0; k < 2; ++k)
+    if (cudaMallocHost(reinterpret_cast<void **>(&pin[k]), size_t(kChunk) * 8) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      release();
+      return set_error(HLR_ERR_OOM, "hlr_upload: pinned staging for device encoding");
+    }
+  int64_t u0 = 0;
+  for (int64_t c0 = 0, k = 0; c0 < total; c0 += kChunk, k ^= 1) {
+    const int64_t c1 = std::min(total, c0 + kChunk);
+    cudaEventSynchronize(done[k]);  // the copy out of this buffer two chunks ago has finished
+    while (voff[u0 + 1] <= c0) ++u0;
+    int64_t u1 = u0;
+    while (u1 < nu && voff[u1] < c1) ++u1;
+    double *buf = pin[k];
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t u = u0; u < u1; ++u) {
+      const int64_t lo = std::max(voff[u], c0), hi = std::min(voff[u + 1], c1);
+      if (hi > lo) std::memcpy(buf + (lo - c0), usrc[u] + (lo - voff[u]), size_t(hi - lo) * 8);
+    }
+    if (cudaMemcpyAsync(a_dev + c0, buf, size_t(c1 - c0) * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(done[k], st) != cudaSuccess) {
+      release();
+      return set_error(HLR_ERR_CUDA, "hlr_upload: copying values for device encoding");
+    }
+  }
+  int rc = HLR_OK;
+  if (cudaMemcpyAsync(off_dev, voff.data(), 8 * size_t(nu + 1), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(u_dev, uprec.data(), 8 * size_t(nu), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = set_error(HLR_ERR_CUDA, "hlr_upload: copying unit offsets for device encoding");
+  if (!rc)
+    rc = hlr_encode_device(fmt, nu, off_dev, total, a_dev, u_dev, mm_dev, e_dev, m_dev, oo_dev, out_dev, cap, st);
+  std::vector<double> mm(nu);
+  std::vector<int32_t> ee(nu), em(nu);
+  std::vector<int64_t> oo(nu + 1);
+  if (!rc && (cudaMemcpyAsync(mm.data(), mm_dev, 8 * size_t(nu), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaMemcpyAsync(ee.data(), e_dev, 4 * size_t(nu), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaMemcpyAsync(em.data(), m_dev, 4 * size_t(nu), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaMemcpyAsync(oo.data(), oo_dev, 8 * size_t(nu + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+              cudaStreamSynchronize(st) != cudaSuccess))
+    rc = set_error(HLR_ERR_CUDA, "hlr_upload: reading device encoding results");
+  release();
+  if (rc) return rc;
+  const int kind = fmt == HLR_FMT_BFL ? VF_BFL : fmt == HLR_FMT_DFL ? VF_DFL : fmt == HLR_FMT_MP ? VF_MP : VF_AFL;
+  prm->resize(nu);
+  uoff->assign(nu + 1, 0);
+  for (int64_t u = 0; u < nu; ++u) {
+    if (ee[u] < 0)
+      return set_error(HLR_ERR_INVALID, "hlr_upload: NaN or Inf in block data (or beyond the format's range)");
+    AflParams &q = (*prm)[u];
+    q.m_min = mm[u];
+    q.e = ee[u];
+    q.m = em[u];
+    q.w = 1 + ee[u] + em[u];
+    q.kind = kind;
+    (*uoff)[u + 1] = (*uoff)[u] + padded16(afl_bytes(len[u], q.w));
+    if (int64_t((*uoff)[u]) != oo[u])
+      return set_error(HLR_ERR_CUDA, "hlr_upload: device encoder offsets differ from the layout");
+  }
+  canon->p = static_cast<uint8_t *>(std::aligned_alloc(64, align_up((*uoff)[nu] + 64, 64)));
+  if (!canon->p) return set_error(HLR_ERR_OOM, "hlr_upload: host allocation failed");
+  std::memset(canon->p + (*uoff)[nu], 0, 64);
+  if (cudaMemcpy(canon->p, out_dev, (*uoff)[nu], cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(HLR_ERR_CUDA, "hlr_upload: reading device encoded streams");
+  return HLR_OK;
+}
+
 }  // namespace
 }  // namespace hlr
 
@@ -84,7 +195,8 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
       d->format != HLR_FMT_BFL && d->format != HLR_FMT_DFL && d->format != HLR_FMT_MP)
     return set_error(HLR_ERR_INVALID, "hlr_upload: unknown format");
   int sub_rows = kSubRows, leaf_rows = kLeafRows, piece_max = kPieceMax;
-  if ((d->tuning >> 16) & ~0xf1) return set_error(HLR_ERR_INVALID, "hlr_upload: unknown tuning flags");
+  if ((d->tuning >> 16) & ~0xf3) return set_error(HLR_ERR_INVALID, "hlr_upload: unknown tuning flags");
+  const bool enc_dev = (d->tuning & HLR_ENCODE_DEVICE) != 0;
   const bool keep_map = (d->tuning & HLR_DECODE_MAP) != 0;
   const int ctas_sm = (d->tuning >> 20) & 15;  // HLR_CTAS_PER_SM; 0: as many as are resident
   if (ctas_sm > 8) return set_error(HLR_ERR_INVALID, "hlr_upload: bad tuning (HLR_CTAS_PER_SM above 8)");
@@ -212,10 +324,20 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     }
   }
   const int64_t nunits = int64_t(usrc.size());
-  in.prm.resize(nunits);
+  HostBuf canon;
+  const bool on_device = afl && enc_dev && nunits > 0;
+  if (on_device) {
+    std::vector<uint64_t> uoff_dev;
+    if (int rc = encode_units_on_device(d->format, usrc, in.unit_len, uprec, static_cast<cudaStream_t>(cuda_stream),
+                                        &in.prm, &uoff_dev, &canon))
+      return rc;
+  } else {
+    in.prm.resize(nunits);
+  }
   int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
   for (int64_t u = 0; u < nunits; ++u) {
+    if (on_device) continue;
     if (afl) {
       if (!unit_params(d->format, usrc[u], in.unit_len[u], uprec[u], &in.prm[u])) bad |= 1;
     } else {
@@ -242,12 +364,14 @@ extern "C" int hlr_upload(const hlr_hmatrix_desc *d, void *cuda_stream, hlr_hand
     stream_bytes += bytes;
     in.uoff[u + 1] = in.uoff[u] + padded16(bytes);
   }
-  HostBuf canon;
-  canon.p = static_cast<uint8_t *>(std::aligned_alloc(64, align_up(in.uoff[nunits] + 64, 64)));
-  if (!canon.p) return set_error(HLR_ERR_OOM, "hlr_upload: host allocation failed");
-  std::memset(canon.p + in.uoff[nunits], 0, 64);
+  if (!on_device) {
+    canon.p = static_cast<uint8_t *>(std::aligned_alloc(64, align_up(in.uoff[nunits] + 64, 64)));
+    if (!canon.p) return set_error(HLR_ERR_OOM, "hlr_upload: host allocation failed");
+    std::memset(canon.p + in.uoff[nunits], 0, 64);
+  }
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t u = 0; u < nunits; ++u) {
+    if (on_device) continue;  // the device encoder wrote the streams, zero-padded to 16 bytes
     uint8_t *dst = canon.p + in.uoff[u];
     std::memset(dst, 0, in.uoff[u + 1] - in.uoff[u]);
     if (afl)
@@ -505,6 +629,7 @@ extern "C" int hlr_free(hlr_handle h) {
   if (H->arena) cudaFree(H->arena);
   if (H->cg_ws) cudaFree(H->cg_ws);
   if (H->multi_ws) cudaFree(H->multi_ws);
+  for (void *w : H->col_ws) cudaFree(w);
   for (void *e : H->prof_ev)
     if (e) cudaEventDestroy(static_cast<cudaEvent_t>(e));
   if (ce != cudaSuccess) return set_error(HLR_ERR_CUDA, std::string("hlr_free: ") + cudaGetErrorString(ce));

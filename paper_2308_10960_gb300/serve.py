@@ -42,7 +42,8 @@ class Request:
     arrival: float = 0.0      # seconds after the start of the run
     rtol: float = 1e-8
     maxit: int = 10000
-    y: Any = None             # result
+    y: Any = None             # result; a device vector of length n given here receives it
+    ready: Any = None         # CUDA event after the client's writes of x (None: x is complete)
     iters: int = 0
     relres: float = 0.0
     start: float | None = None
@@ -244,33 +245,55 @@ class Server:
 
 class GpuBackend:
     """Drives the library. `host_mats` maps names to objects with ``upload(fmt, stream=...)``
-    returning a DeviceHMatrix (HostHMatrix, or any adapter); they are uploaded on admission."""
+    returning a DeviceHMatrix (HostHMatrix, or any adapter); they are uploaded on admission.
 
-    def __init__(self, host_mats: dict, acc_cg: str = "fp32", solve_share: int = 4):
+    Nothing on the request path allocates device memory, creates CUDA objects or touches the
+    legacy default stream: the streams, events and per-matrix staging buffers are made up front
+    (at construction and on admission), because those calls can wait for work on other streams
+    and stall the serving loop for as long as the solves keep the GPU busy (measured: an event
+    recorded on the default stream held a product batch for seconds). A request's x must be
+    complete when it is submitted, or carry in ``ready`` an event recorded after its writes. A
+    request whose ``y`` is a device vector of length n (the client's output buffer) gets its
+    result written there; otherwise one is allocated for it."""
+
+    def __init__(self, host_mats: dict, acc_cg: str = "fp32", solve_share: int = 4, max_rhs: int = 32,
+                 cg_workers: int = 4, events: int = 256, tunings: dict | None = None):
         import torch
         from . import matvec_batched
         self.torch = torch
         self._batched = matvec_batched
         self.host = dict(host_mats)
+        self.tunings = dict(tunings or {})   # name -> tuning code of its upload (e.g. autotuned)
         self.dev = {}
         self.acc_cg = acc_cg
+        self.max_rhs = int(max_rhs)
         # solves run their product kernels on solve_share eighths of the CTA slots
         # (HLR_SM_SHARE), so that product batches find room on every SM while solves run
         self.solve_share = int(solve_share)
         # product batches on a high-priority stream: their CTAs are scheduled ahead of the
         # solves' kernels, so a short product does not queue behind long CG runs
         self.stream = torch.cuda.Stream(priority=-1)
+        self._solve_streams = [torch.cuda.Stream() for _ in range(max(1, cg_workers))]
+        self._free_streams = list(range(len(self._solve_streams)))
+        self._lock = threading.Lock()
+        # events, created (first recorded) here: product-batch completion tokens, input order
+        # for the product stream and one per solve stream
+        self._events = [torch.cuda.Event() for _ in range(events)]
+        for e in self._events:
+            e.record(self.stream)
+        self._free_events = list(range(events))
+        self._staging = {}
         self._bytes = {}
         self._alg = {}
-        self._local = threading.local()
         for name, H in self.host.items():     # device footprint and algorithmic bytes, measured once
             A = H.upload("afl")
             self._bytes[name] = int(A.info["device_bytes"])
             self._alg[name] = (float(A.info["algorithmic_bytes"]), int(A.info["n"]))
             A.free()
+        torch.cuda.synchronize()
 
     def device_bytes(self, name: str) -> int:
-        return self._bytes[name]
+        return self._bytes[name] + 2 * 8 * self.max_rhs * self._alg[name][1]
 
     def product_bytes(self, name: str, r: int) -> float:
         alg, n = self._alg[name]
@@ -278,49 +301,84 @@ class GpuBackend:
 
     def load(self, name: str):
         if name not in self.dev:          # a later run on the same backend finds it resident
-            self.dev[name] = self.host[name].upload("afl", stream=self.stream)
+            torch = self.torch
+            n = self._alg[name][1]
+            with torch.cuda.stream(self.stream):
+                code = self.tunings.get(name, 0)
+                self.dev[name] = (self.host[name].upload("afl", stream=self.stream, tuning=code) if code
+                                  else self.host[name].upload("afl", stream=self.stream))
+                X, Y = (torch.zeros((self.max_rhs, n), dtype=torch.float64, device="cuda"),
+                        torch.zeros((self.max_rhs, n), dtype=torch.float64, device="cuda"))
+                self._staging[name] = (X, Y)
+                # one full-width batch now, so that the per-column scratch sets exist before any
+                # request (the library allocates them on first use)
+                self._batched([self.dev[name]], [X], [Y], acc="fp32", stream=self.stream, multi=True)
+                Y.zero_()
 
     def unload(self, name: str):
         if name in self.dev:
             self.dev.pop(name).free()
+            self._staging.pop(name, None)
 
     def launch_matvecs(self, groups):
         torch = self.torch
         mats, Xs, Ys = [], [], []
-        self.stream.wait_stream(torch.cuda.default_stream())   # inputs were written there
         with torch.cuda.stream(self.stream):
             for name, reqs in groups:
-                for r in reqs:
-                    r.x.record_stream(self.stream)
-                X = torch.stack([r.x for r in reqs]) if len(reqs) > 1 else reqs[0].x.view(1, -1)
-                Y = torch.zeros_like(X)
+                X, Y = self._staging[name]
+                k = len(reqs)
+                for i, r in enumerate(reqs):
+                    if r.ready is not None:
+                        self.stream.wait_event(r.ready)
+                    X[i].copy_(r.x)
+                Y[:k].zero_()
                 mats.append(self.dev[name])
-                Xs.append(X)
-                Ys.append(Y)
+                Xs.append(X[:k])
+                Ys.append(Y[:k])
             self._batched(mats, Xs, Ys, acc="fp32", stream=self.stream, multi=True)
-            ev = torch.cuda.Event()
+            for (name, reqs), Y in zip(groups, Ys):
+                for i, r in enumerate(reqs):
+                    if r.y is None:
+                        r.y = torch.empty_like(r.x)
+                    r.y.copy_(Y[i])
+            with self._lock:
+                idx = self._free_events.pop() if self._free_events else None
+            ev = self._events[idx] if idx is not None else torch.cuda.Event()
             ev.record(self.stream)
-        for (name, reqs), Y in zip(groups, Ys):
-            for i, r in enumerate(reqs):
-                r.y = Y[i]
-        return ev
+        return (ev, idx)
 
     def poll(self, token) -> bool:
-        return token.query()
+        ev, idx = token
+        if not ev.query():
+            return False
+        if idx is not None:
+            with self._lock:
+                self._free_events.append(idx)
+        return True
 
     def solve(self, name: str, r: Request):
         torch = self.torch
-        s = getattr(self._local, "stream", None)
-        if s is None:
-            s = self._local.stream = torch.cuda.Stream()
-        A = self.dev[name]
-        s.wait_stream(torch.cuda.default_stream())
-        with torch.cuda.stream(s):
-            x = torch.zeros_like(r.x)
-            r.iters, r.relres = A.solve_cg(r.x, x, rtol=r.rtol, maxit=r.maxit, acc=self.acc_cg, stream=s,
-                                           raise_noconv=False, sm_share=self.solve_share)
-        s.synchronize()
-        r.y = x
+        with self._lock:                  # a solve holds one of the solve streams while it runs
+            if not self._free_streams:    # more concurrent solves than streams made up front
+                self._solve_streams.append(torch.cuda.Stream())
+                self._free_streams.append(len(self._solve_streams) - 1)
+            k = self._free_streams.pop()
+        try:
+            s = self._solve_streams[k]
+            A = self.dev[name]
+            if r.ready is not None:
+                s.wait_event(r.ready)
+            with torch.cuda.stream(s):
+                if r.y is None:
+                    r.y = torch.zeros_like(r.x)
+                else:
+                    r.y.zero_()
+                r.iters, r.relres = A.solve_cg(r.x, r.y, rtol=r.rtol, maxit=r.maxit, acc=self.acc_cg, stream=s,
+                                               raise_noconv=False, sm_share=self.solve_share)
+            s.synchronize()
+        finally:
+            with self._lock:
+                self._free_streams.append(k)
 
     def drain(self):
         self.torch.cuda.synchronize()

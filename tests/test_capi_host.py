@@ -143,6 +143,7 @@ def test_tuning_codes_and_rejection():
     assert hg.tuning_code(32, 64, 16) == 5 | (6 << 4) | (16 << 8)
     assert hg.tuning_code(128, 32, 8) == 7 | (5 << 4) | (8 << 8)
     assert "#define HLR_CTAS_PER_SM(k) ((k) << 20)" in hdr
+    assert "#define HLR_ENCODE_DEVICE (1 << 17)" in hdr and hg.HLR_ENCODE_DEVICE == 1 << 17
     assert hg.tuning_code(ctas_per_sm=3) == 3 << 20
     assert hg.tuning_code(32, 64, 16, 2) == 5 | (6 << 4) | (16 << 8) | (2 << 20)
     with pytest.raises(hg.HlrError):
@@ -151,7 +152,7 @@ def test_tuning_codes_and_rejection():
         hg.tuning_code(ctas_per_sm=9)
     bl = _tiny_blocks()
     for bad in [3 | (6 << 4) | (16 << 8), 6 | (7 << 4) | (16 << 8), 6 | (6 << 4) | (2 << 8), 6 | (6 << 4) | (17 << 8),
-                -1, 1 << 17, 9 << 20, 1 << 24]:
+                -1, 1 << 18, 1 << 19, 9 << 20, 1 << 24]:
         with pytest.raises(hg.HlrError, match="tuning"):
             hg.upload(5, None, bl, 1e-6, tuning=bad)
     with pytest.raises(hg.HlrError, match="tuning"):

@@ -119,3 +119,40 @@ def test_encode_device_rounding_boundaries(fmt):
     np.cumsum([x.size for x in units], out=off[1:])
     ref = [afl.encode(x, p, fmt) for x, p in zip(units, precs)]
     _check_units(vals, off, np.array(precs), fmt, ref)
+
+
+@pytest.mark.parametrize("fmt", FMTS)
+def test_upload_with_device_encoding_is_the_same_matrix(fmt, exp2d_case):
+    """HLR_ENCODE_DEVICE (compression on the GPU during the upload, Section 5.3) gives the
+    matrix the host encoder gives: the same decoded values and the same products, bit for bit,
+    and the same stored byte counts."""
+    p, H, C = exp2d_case
+    A = hg.upload(p.n, H.perm, oracle_blocks(H), H.eps, fmt=fmt)
+    D = hg.upload(p.n, H.perm, oracle_blocks(H), H.eps, fmt=fmt, tuning=hg.HLR_ENCODE_DEVICE)
+    try:
+        for k in ("stream_bytes", "header_bytes", "algorithmic_bytes", "nunits", "values"):
+            assert A.info[k] == D.info[k], k
+        da = torch.empty(A.info["values"], dtype=torch.float64, device="cuda")
+        dd = torch.empty_like(da)
+        A.decode_units(da)
+        D.decode_units(dd)
+        assert torch.equal(da.view(torch.int64), dd.view(torch.int64))
+        x = torch.from_numpy(np.random.default_rng(5).standard_normal(p.n)).cuda()
+        for acc in ("fp32", "fp64"):
+            ya = torch.zeros(p.n, dtype=torch.float64, device="cuda")
+            yd = torch.zeros_like(ya)
+            A.matvec(x, ya, acc=acc)
+            D.matvec(x, yd, acc=acc)
+            A.check()
+            D.check()
+            assert torch.equal(ya.view(torch.int64), yd.view(torch.int64)), acc
+    finally:
+        A.free()
+        D.free()
+
+
+def test_upload_with_device_encoding_rejects_non_finite():
+    bl = [{"row0": 0, "nrows": 4, "col0": 0, "ncols": 4, "kind": hg.HLR_DENSE,
+           "D": np.array([[1.0, 2.0, np.nan, 3.0]] * 4)}]
+    with pytest.raises(hg.HlrError, match="NaN or Inf"):
+        hg.upload(4, None, bl, 1e-6, tuning=hg.HLR_ENCODE_DEVICE)

@@ -59,9 +59,12 @@ class _Host:
 
 def test_autotuner_picks_a_candidate(exp2d_case):
     p, H, C = exp2d_case
-    t = tune.Autotuner(candidates=[(64, 64, 16), (32, 64, 16), (64, 32, 8)], reps=5)
-    for nrhs in (1, 8):
+    t = tune.Autotuner(candidates=[(64, 64, 16), (32, 64, 16), (64, 32, 8), (64, 64, 16, 3)], reps=5)
+    for nrhs in (1, 8, 32):
         res = t.tune(_Host(p, H), nrhs=nrhs)
         assert res.best in t.candidates and set(res.ms) == set(t.candidates)
         assert all(v > 0 for v in res.ms.values())
         assert t.table[res.rank_class] == res.best
+    # a second matrix of a known class takes the stored choice without timing
+    code, rc, res = t.choose(_Host(p, H), nrhs=8)
+    assert res is None and code == hg.tuning_code(*t.table[rc])
