@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--acc", default="fp32", choices=["fp32", "fp64"],
                     help="accumulation of the headline product: fp32 in-block / fp64 across blocks (default), "
                          "or fp64 throughout (the paper's arithmetic)")
-    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve", "small", "scale"],
+    ap.add_argument("--workload", default="laplace", choices=["laplace", "batch48", "serve", "small", "scale", "multi"],
                     help="laplace: one n=262144 sphere matrix (default); batch48: 48 Matern matrices of "
                          "uneven size with 1/8/32 right-hand sides in one batched launch sequence; serve: "
                          "Poisson requests (70%% products, 30%% CG solves) against resident Matern matrices; "
@@ -905,6 +905,58 @@ def run_scale(args, world: int, rank: int, local: int):
     A.free()
 
 
+def run_multi(args, world: int, rank: int, local: int):
+    """Multi-column products on the --n Laplace sphere: one single-column product, then one
+    hlr_matvec_batched request of 8 and of 32 columns (narrow and wide passes), with the default
+    work lists and with lists made for the passes' 3 CTAs per SM (HLR_CTAS_PER_SM(3)). value =
+    algorithmic bytes of the 32-column request / its time with the better shape; --steps timed
+    calls each after --warmup."""
+    import torch
+    import synth
+    import paper_2308_10960_gb300 as hg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prob = synth.laplace_problem(args.n)
+    Hh = hg.build_kernel_hmatrix(prob.points, "laplace", args.eps, diag=prob.params["diag"], eta=2.0, leaf_size=64)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.from_numpy(synth.rhs(args.n, 1)).to(dev)
+    res = {}
+    best = None
+    for shape in (0, 3):
+        A = Hh.upload("afl", tuning=hg.tuning_code(ctas_per_sm=shape))
+        info = A.info
+        y = torch.zeros(args.n, dtype=torch.float64, device=dev)
+        for _ in range(max(3, args.warmup)):
+            A.matvec(x, y, acc="fp32", stream=stream)
+        t1 = time_loop(lambda: A.matvec(x, y, acc="fp32", stream=stream), args.steps, stream) / args.steps
+        row = {"single_ms": t1 * 1e3}
+        for r in (8, 32):
+            X = torch.from_numpy(synth.rhs(args.n * r, 2 + r)).to(dev).view(r, args.n)
+            Y = torch.zeros((r, args.n), dtype=torch.float64, device=dev)
+            for _ in range(max(3, args.warmup)):
+                hg.matvec_batched([A], [X], [Y], acc="fp32", stream=stream)
+            tm = time_loop(lambda: hg.matvec_batched([A], [X], [Y], acc="fp32", stream=stream), args.steps,
+                           stream) / args.steps
+            bm = multi_rhs_bytes(info, args.n, r)
+            row[str(r)] = {"ms": tm * 1e3, "GB/s": bm / tm / 1e9, "vs_one_single": tm / t1,
+                           "speedup_vs_r_single_products": r * t1 / tm}
+            if r == 32 and (best is None or tm < best[0]):
+                best = (tm, bm)
+            del X, Y
+        A.check()
+        A.free()
+        res[f"ctas_per_sm={shape or 'default'}"] = row
+    if rank == 0:
+        out = {"metric": METRIC, "value": best[1] / best[0] / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": best[0] * 1e3, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"laplace-sphere n={args.n} eps={args.eps:g}, 32 right-hand sides per request",
+                          "n": args.n, "eps": args.eps}, "multi_rhs": res}
+        print(json.dumps(out), flush=True)
+    Hh.free()
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -928,6 +980,8 @@ def main():
         run_small(args, world, rank, local)
     elif args.workload == "scale":
         run_scale(args, world, rank, local)
+    elif args.workload == "multi":
+        run_multi(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -586,7 +586,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
                                uint64_t *empty) {
   using A = typename Tr<FMT>::A;
   constexpr size_t slot = slot_bytes<FMT, 0>();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -725,7 +725,7 @@ __device__ bool consume_phase1_pairs(const DevLayout &L, uint32_t np, uint32_t &
                                      uint64_t *empty) {
   constexpr int FMT = FMT_AFL32;
   constexpr size_t slot = slot_bytes<FMT, 0>();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -1246,7 +1246,7 @@ __device__ bool consume_phase1_f64(const DevLayout &L, uint32_t np, uint32_t &it
                                    uint64_t *empty) {
   constexpr int FMT = FMT_AFL64;
   constexpr size_t slot = slot_bytes<FMT, 0>();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
@@ -1549,7 +1549,7 @@ __device__ bool consume_phase1_multi_fma(const Job &jb, uint32_t np, uint32_t &i
                                      uint64_t *empty) {
   const DevLayout &L = jb.L;
   constexpr size_t slot = slot_bytes<FMT_AFL32, 0, R>();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
@@ -1631,42 +1631,44 @@ __device__ bool consume_phase1_multi_fma(const Job &jb, uint32_t np, uint32_t &i
 }
 
 // ---------------------------------------------------------------------------------------------
-// Multi-RHS pass, phase 1 on the tensor cores: for every segment (the X columns of one item of a
-// lowrank block) T^T(R x columns) = X_perm^T(R x rows) X~(rows x columns). Every lane decodes its
-// slice (rows sub, sub + G, ... of one column) into a padded shared-memory tile of its warp (64
-// values per lane and round); then, per segment present in the warp, the warp runs the
-// contraction over the segment's rows in steps of 8: the right-hand sides are the M dimension
-// (R / 16 tiles of 16, or one half-filled tile for R = 8), read from X_perm once per step and
-// segment (8 rows x 16 right-hand sides, one 32-byte sector per row), and up to 32 of the
-// segment's columns in the warp are the N dimension (tiles of 8; row rho of column c is in lane
-// c + rho % G at position rho / G of the tile). Every column's G lanes lie in one warp, so a warp
-// completes the dot products of its columns. A column's T (times its factor), or its chunk
-// partial sum, is written from the C fragments.
+// Multi-RHS pass of up to 32 columns, phase 1: every lane decodes its slice (rows sub, sub + G,
+// ... of one column) into a padded shared-memory tile of its warp (64 values per lane and
+// round). Then, per segment present in the warp (the X columns of one item of a lowrank block),
+// the warp's lanes take (column, row phase, group of 16 right-hand sides) triples: a lane walks
+// the rows p, p + P, ... of its column, reads each decoded value from the tile and the row's 16
+// x values from X_perm, and keeps 16 FP32 dot products. All lanes of a step read few distinct x
+// rows (every column of the segment shares them), so an x row is loaded once per warp and step
+// instead of once per value; the P row phases of a column are added with xor-shuffles in fixed
+// order. Every column's G lanes lie in one warp, so a warp completes its columns. The result,
+// times the column factor (one chunk) or as a chunk partial sum, is written per column.
 // ---------------------------------------------------------------------------------------------
 template <int R>
 __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, uint8_t *smem, uint64_t *full,
                                      uint64_t *empty, float *tiles) {
+  static_assert(R % 16 == 0, "wide pass: groups of 16 right-hand sides");
   const DevLayout &L = jb.L;
   constexpr size_t slot = slot_bytes<FMT_AFL32, 0, R>();
-  constexpr int kVS = 65;            // values per lane in the tile (64) + 1: conflict-free stores by row
-  constexpr int MT = (R + 15) / 16;  // M tiles of right-hand sides
+  constexpr int kVS = 65;           // values per lane in the tile (64) + 1: conflict-free stores by row
+  constexpr int NQ = R / 16;        // groups of 16 right-hand sides
+  constexpr int SL = 32 / NQ;       // (column, row phase) slots of a warp
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int g = lane >> 2, tq = lane & 3;
+  const int q = lane % NQ, sl = lane / NQ;
   float *tv = tiles + warp * (32 * kVS + 64);                 // [32 lanes][kVS] decoded values
   int *clane = reinterpret_cast<int *>(tv + 32 * kVS);        // [32] lanes of a segment's columns
   int *cj = clane + 32;                                       // [32] their column indices j
+  const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   for (uint32_t i = 0; i < np; ++i, ++it) {
     const uint32_t s = it % kStages;
     if (!mbar_wait(&full[s], (it / kStages) & 1)) {
       atomicOr(L.status, 1u);
       return false;
     }
-    const uint8_t *sl = smem + size_t(s) * slot;
-    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl);
-    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl);
-    const Seg *segs = reinterpret_cast<const Seg *>(sl + 16);
+    const uint8_t *sl_p = smem + size_t(s) * slot;
+    const uint32_t *Wd = reinterpret_cast<const uint32_t *>(sl_p);
+    const PieceHdr *ph = reinterpret_cast<const PieceHdr *>(sl_p);
+    const Seg *segs = reinterpret_cast<const Seg *>(sl_p + 16);
     LaneHdr h{0xff, 0, 0, 0};
-    if (t < int(ph->ncols)) h = lane_hdrs(sl, ph)[t];
+    if (t < int(ph->ncols)) h = lane_hdrs(sl_p, ph)[t];
     const bool active = h.seg != 0xff;
     int sub = 0, rc = 0;
     const uint32_t *col = Wd;
@@ -1705,89 +1707,72 @@ __device__ bool consume_phase1_multi(const Job &jb, uint32_t np, uint32_t &it, u
       const Seg &sg = segs[s0];
       const int lg = sg.lg, gm = (1 << lg) - 1, nr = sg.nr;
       const int ncol = __popc(mask);
-      const int nnt = (ncol + 7) >> 3;  // N tiles of 8 columns (1..4)
       if (mine) {
         const int k = __popc(mask & ((1u << lane) - 1));
         clane[k] = lane;
         cj[k] = h.j;
       }
       __syncwarp();
-      // this lane's B columns: column g of every N tile (-1: none)
-      int lc[4];
+      for (int c0 = 0; c0 < ncol; c0 += SL) {  // columns in chunks of SL (more than one only if G = 1)
+        const int cc = min(SL, ncol - c0);
+        int lcp = 0;
+        while ((1 << lcp) < cc) ++lcp;       // column slots: the next power of two >= cc
+        const int cp = 1 << lcp, P = SL >> lcp;
+        const int cl = sl & (cp - 1), p = sl >> lcp;
+        const bool on = cl < cc;
+        const int lc = on ? clane[c0 + cl] : 0;
+        float acc[16];
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) lc[nt] = 8 * nt + g < ncol ? clane[8 * nt + g] : -1;
-      float acc[MT][4][4];
-#pragma unroll
-      for (int m = 0; m < MT; ++m)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[m][nt][e] = 0.f;
-      const float *xrow = jb.xp + size_t(sg.gx) * R;
-      for (int rb = 0; rb < nr; rb += 64 << lg) {  // rounds of 64 positions per lane
-        if (rb > 0) {  // a later round (slices longer than 64 rows): this segment's lanes decode it
-          __syncwarp();
-          if (segme == s0) decode_round(rb >> lg);
-          __syncwarp();
-        }
-        const int rend = min(nr, rb + (64 << lg));
-        for (int rho = rb; rho < rend; rho += 8) {
-          const int r0 = rho + tq, r1 = rho + tq + 4;
-          const bool ok0 = r0 < nr, ok1 = r1 < nr;
-          // A = X_perm^T: (right-hand side 16 m + g (+ 8), row r0 / r1)
-          uint32_t ah[MT][4], al[MT][4];
-#pragma unroll
-          for (int m = 0; m < MT; ++m) {
-            const int q0 = 16 * m + g, q1 = 16 * m + g + 8;
-            const float a0 = ok0 ? __ldg(xrow + size_t(r0) * R + q0) : 0.f;
-            const float a1 = (ok0 && q1 < R) ? __ldg(xrow + size_t(r0) * R + q1) : 0.f;
-            const float a2 = ok1 ? __ldg(xrow + size_t(r1) * R + q0) : 0.f;
-            const float a3 = (ok1 && q1 < R) ? __ldg(xrow + size_t(r1) * R + q1) : 0.f;
-            tf32_split(a0, ah[m][0], al[m][0]);
-            tf32_split(a1, ah[m][1], al[m][1]);
-            tf32_split(a2, ah[m][2], al[m][2]);
-            tf32_split(a3, ah[m][3], al[m][3]);
+        for (int e = 0; e < 16; ++e) acc[e] = 0.f;
+        for (int rb = 0; rb < nr; rb += 64 << lg) {  // rounds of 64 positions per lane
+          if (rb > 0) {  // slices longer than 64 rows (one column chunk then): decode the next round
+            __syncwarp();
+            if (segme == s0) decode_round(rb >> lg);
+            __syncwarp();
           }
-          const int p0 = (r0 - rb) >> lg, p1 = (r1 - rb) >> lg, s0l = r0 & gm, s1l = r1 & gm;
-#pragma unroll
-          for (int nt = 0; nt < 4; ++nt) {
-            if (nt >= nnt) break;
-            // B = X~: (row r0 / r1, column 8 nt + g)
-            const float b0 = (ok0 && lc[nt] >= 0) ? tv[(lc[nt] + s0l) * kVS + p0] : 0.f;
-            const float b1 = (ok1 && lc[nt] >= 0) ? tv[(lc[nt] + s1l) * kVS + p1] : 0.f;
-            uint32_t bh0, bl0, bh1, bl1;
-            tf32_split(b0, bh0, bl0);
-            tf32_split(b1, bh1, bl1);
-#pragma unroll
-            for (int m = 0; m < MT; ++m) mma3_add(acc[m][nt], ah[m], al[m], bh0, bh1, bl0, bl1);
+          const int rend = min(nr, rb + (64 << lg));
+          if (on) {
+#pragma unroll 4
+            for (int rho = rb + p; rho < rend; rho += P) {  // unrolled: loads of 4 rows in flight
+              const float v = tv[(lc + (rho & gm)) * kVS + ((rho - rb) >> lg)];
+              const float4 *xr = xp4 + (size_t(sg.gx) + rho) * (R / 4) + 4 * q;
+              const float4 x0 = __ldg(xr), x1 = __ldg(xr + 1), x2 = __ldg(xr + 2), x3 = __ldg(xr + 3);
+              acc[0] = fmaf(v, x0.x, acc[0]);
+              acc[1] = fmaf(v, x0.y, acc[1]);
+              acc[2] = fmaf(v, x0.z, acc[2]);
+              acc[3] = fmaf(v, x0.w, acc[3]);
+              acc[4] = fmaf(v, x1.x, acc[4]);
+              acc[5] = fmaf(v, x1.y, acc[5]);
+              acc[6] = fmaf(v, x1.z, acc[6]);
+              acc[7] = fmaf(v, x1.w, acc[7]);
+              acc[8] = fmaf(v, x2.x, acc[8]);
+              acc[9] = fmaf(v, x2.y, acc[9]);
+              acc[10] = fmaf(v, x2.z, acc[10]);
+              acc[11] = fmaf(v, x2.w, acc[11]);
+              acc[12] = fmaf(v, x3.x, acc[12]);
+              acc[13] = fmaf(v, x3.y, acc[13]);
+              acc[14] = fmaf(v, x3.z, acc[14]);
+              acc[15] = fmaf(v, x3.w, acc[15]);
+            }
           }
         }
-      }
-      // C(right-hand side, column): this lane holds right-hand sides 16 m + g (+ 8) of columns
-      // 8 nt + 2 tq and 8 nt + 2 tq + 1
+        // the P row phases of a column (lanes whose slot differs in the bits above lcp)
+        for (int o = cp * NQ; o < 32; o <<= 1) {
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        if (nt >= nnt) break;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int k = 8 * nt + 2 * tq + cc;
-          if (k >= ncol) continue;
-          const int j = cj[k];
+          for (int e = 0; e < 16; ++e) acc[e] += __shfl_xor_sync(kFull, acc[e], o);
+        }
+        if (on && p == 0) {
+          const int j = cj[c0 + cl];
           if (sg.x.nchunks == 1) {
             const float f = __ldg(L.fac32 + sg.tidx + j);
-            float *dst = jb.tw + (size_t(sg.tidx) + j) * R;
+            float4 *dst = reinterpret_cast<float4 *>(jb.tw + (size_t(sg.tidx) + j) * R + 16 * q);
 #pragma unroll
-            for (int m = 0; m < MT; ++m) {
-              dst[16 * m + g] = acc[m][nt][cc] * f;
-              if (16 * m + g + 8 < R) dst[16 * m + g + 8] = acc[m][nt][2 + cc] * f;
-            }
+            for (int e = 0; e < 4; ++e)
+              dst[e] = make_float4(acc[4 * e] * f, acc[4 * e + 1] * f, acc[4 * e + 2] * f, acc[4 * e + 3] * f);
           } else {
-            double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * R;
+            double *dst = jb.part + (size_t(sg.x.pbase) + size_t(j) * sg.x.nchunks + sg.x.chunk) * R + 16 * q;
 #pragma unroll
-            for (int m = 0; m < MT; ++m) {
-              dst[16 * m + g] = double(acc[m][nt][cc]);
-              if (16 * m + g + 8 < R) dst[16 * m + g + 8] = double(acc[m][nt][2 + cc]);
-            }
+            for (int e = 0; e < 16; ++e) dst[e] = double(acc[e]);
           }
         }
       }
