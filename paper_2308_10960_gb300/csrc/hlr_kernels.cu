@@ -701,7 +701,7 @@ __device__ bool consume_phase1(const DevLayout &L, uint32_t np, uint32_t &it, ui
 // of their rows, summed in two FP32 partial sums (even and odd values). An odd last value comes
 // with the next (unused) code of its window; windows read at most two rows of 32 words past the
 // slice (inside the pad).
-template <bool WIDE>
+template <bool WIDE, bool MID = false>
 __device__ __forceinline__ float p1_pairs(int rc, uint32_t col_s, const ColDec &c, uint32_t xa, uint32_t xstep) {
   float s0 = 0.f, s1 = 0.f;
   uint32_t b = 0;
@@ -710,13 +710,13 @@ __device__ __forceinline__ float p1_pairs(int rc, uint32_t col_s, const ColDec &
   for (; r + 2 <= rc; r += 2, b += 2 * c.w, xa += 2 * xstep) {
     uint32_t c0, c1;
     code_pair<WIDE>(col_s, b, c.w, c0, c1);
-    s0 = fmaf(dec_f32(c0, c), ld_shared_f32(xa), s0);
-    s1 = fmaf(dec_f32(c1, c), ld_shared_f32(xa + xstep), s1);
+    s0 = fmaf(MID ? dec_mid32(c0, c) : dec_f32(c0, c), ld_shared_f32(xa), s0);
+    s1 = fmaf(MID ? dec_mid32(c1, c) : dec_f32(c1, c), ld_shared_f32(xa + xstep), s1);
   }
   if (r < rc) {
     uint32_t c0, c1;
     code_pair<WIDE>(col_s, b, c.w, c0, c1);
-    s0 = fmaf(dec_f32(c0, c), ld_shared_f32(xa), s0);
+    s0 = fmaf(MID ? dec_mid32(c0, c) : dec_f32(c0, c), ld_shared_f32(xa), s0);
   }
   return s0 + s1;
 }
@@ -757,6 +757,8 @@ __device__ bool consume_phase1_pairs(const DevLayout &L, uint32_t np, uint32_t &
       const uint32_t xa = smem_u32(aux + sg.xs + sub), xstep = 4u * G;
       if (c.fast32) {
         dot = narrow ? p1_pairs<false>(rc, smem_u32(col), c, xa, xstep) : p1_pairs<true>(rc, smem_u32(col), c, xa, xstep);
+      } else if (c.mid32 && c.w <= 31) {  // mantissas wider than FP32's, two codes per window
+        dot = p1_pairs<true, true>(rc, smem_u32(col), c, xa, xstep);
       } else {
         const float *xr = aux + sg.xs + sub;
         uint32_t bit = 0;
@@ -979,7 +981,7 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
 // row sum that is never stored.
 static_assert(8 * 128 <= kSlotPad + kAuxMax2 * 4, "phase-2 window reads stay inside the slot");
 
-template <bool WIDE>
+template <bool WIDE, bool MID = false>
 __device__ __forceinline__ void p2_pairs(float (&acc)[64], int nr, uint32_t col_s, const ColDec &c, float mult) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -991,8 +993,13 @@ __device__ __forceinline__ void p2_pairs(float (&acc)[64], int nr, uint32_t col_
       if (!whole && 2 * p >= nr) break;
       uint32_t c0, c1;
       code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
-      acc[2 * p] += dec_mul_f32(c0, c, mult);
-      acc[2 * p + 1] += dec_mul_f32(c1, c, mult);
+      if constexpr (MID) {  // the products p2_rows<1> forms
+        acc[2 * p] += dec_mid32(c0, c) * mult;
+        acc[2 * p + 1] += dec_mid32(c1, c) * mult;
+      } else {
+        acc[2 * p] += dec_mul_f32(c0, c, mult);
+        acc[2 * p + 1] += dec_mul_f32(c1, c, mult);
+      }
     }
   }
 }
@@ -1045,8 +1052,11 @@ __device__ bool consume_phase2_pairs(const DevLayout &L, uint32_t np, uint32_t &
     } else {
       // mantissas wider than FP32's: the FP64 route's values from FP32 operations
       const bool mid = __all_sync(kFull, !active || c.mid32);
+      const bool midp = mid && __all_sync(kFull, !active || c.w <= 31);
       if (active) {
-        if (mid)
+        if (midp)
+          p2_pairs<true, true>(acc, nr, smem_u32(col), c, mult);  // two codes per window
+        else if (mid)
           p2_rows<1, FMT>(acc, nr, col, c, mult);
         else
           p2_rows<2, FMT>(acc, nr, col, c, mult);
@@ -1104,6 +1114,20 @@ __device__ __forceinline__ double vm1_f64(uint32_t code, const ColDec &c) {
   const float v = __uint_as_float((code & c.em_mask) * c.scale + 0x3F800000u) - 1.0f;
   return f32pat_to_f64(__float_as_uint(v));
 }
+// v - 1 exactly in FP64, with integer operations only, for a code of w <= 31 bits whose field is
+// below 16 (e <= 4) and whose mantissa may be wider than FP32's (m up to 30): N = (v - 1) 2^m =
+// (2^m + mant) 2^field - 2^m is an integer below 2^47, so normalising it gives the exact pattern
+// (the value the FP64 route RN(v - 1) gives, since fewer than 53 bits are significant)
+__device__ __forceinline__ double vm1_f64_mid(uint32_t code, const ColDec &c) {
+  const uint32_t m = c.m;
+  const uint32_t mant = m ? (code & (0xffffffffu >> (32 - m))) : 0u;
+  const uint32_t field = (code >> m) & ((1u << c.e) - 1u);
+  const uint64_t N = (((uint64_t(1) << m) + mant) << field) - (uint64_t(1) << m);
+  if (N == 0) return 0.0;
+  const int msb = 63 - __clzll(static_cast<long long>(N));
+  const uint64_t frac = (N << (52 - msb)) & 0xFFFFFFFFFFFFFull;
+  return __longlong_as_double(static_cast<long long>((uint64_t(msb - int(m) + 1023) << 52) | frac));
+}
 // +-s with the code's sign
 __device__ __forceinline__ double signed_f64(uint32_t code, const ColDec &c, double s) {
   return __hiloint2double(__double2hiint(s) ^ int((code << c.sshift) & 0x80000000u), __double2loint(s));
@@ -1112,7 +1136,7 @@ __device__ __forceinline__ double signed_f64(uint32_t code, const ColDec &c, dou
 // Phase 2, FP64 accumulation, AFL codes: one lane per column slice of the leaf, FP64 row sums
 // in registers (one multiply-add per value), a butterfly over the warp and the four warps'
 // sums into ysum at the end of the leaf (as consume_phase2_pairs).
-template <bool WIDE>
+template <bool WIDE, bool MID = false>
 __device__ __forceinline__ void p2_pairs64(double (&acc)[64], int nr, uint32_t col_s, const ColDec &c, double mult) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -1124,8 +1148,10 @@ __device__ __forceinline__ void p2_pairs64(double (&acc)[64], int nr, uint32_t c
       if (!whole && 2 * p >= nr) break;
       uint32_t c0, c1;
       code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
-      acc[2 * p] = fma(vm1_f64(c0, c), signed_f64(c0, c, mult), acc[2 * p]);
-      acc[2 * p + 1] = fma(vm1_f64(c1, c), signed_f64(c1, c, mult), acc[2 * p + 1]);
+      const double v0 = MID ? vm1_f64_mid(c0, c) : vm1_f64(c0, c);
+      const double v1 = MID ? vm1_f64_mid(c1, c) : vm1_f64(c1, c);
+      acc[2 * p] = fma(v0, signed_f64(c0, c, mult), acc[2 * p]);
+      acc[2 * p + 1] = fma(v1, signed_f64(c1, c, mult), acc[2 * p + 1]);
     }
   }
 }
@@ -1184,6 +1210,9 @@ __device__ bool consume_phase2_f64(const DevLayout &L, uint32_t np, uint32_t &it
       if (active) p2_pairs64<false>(acc, nr, smem_u32(col), c, mult);
     } else if (__all_sync(kFull, !active || c.fast32)) {
       if (active) p2_pairs64<true>(acc, nr, smem_u32(col), c, mult);
+    } else if (__all_sync(kFull, !active || (c.mid32 && c.w <= 31))) {
+      // mantissas wider than FP32's: the exact v - 1 from integer operations, two codes per window
+      if (active) p2_pairs64<true, true>(acc, nr, smem_u32(col), c, mult);
     } else if (active) {
       p2_rows64(acc, nr, col, c, mult);
     }
@@ -1222,7 +1251,7 @@ __device__ bool consume_phase2_f64(const DevLayout &L, uint32_t np, uint32_t &it
 
 // Phase 1, FP64 accumulation, AFL codes: the lane's values times the staged FP64 x of their rows,
 // one multiply-add per value into two FP64 partial sums.
-template <bool WIDE>
+template <bool WIDE, bool MID = false>
 __device__ __forceinline__ double p1_pairs64(int rc, uint32_t col_s, const ColDec &c, const double *xr, int xs) {
   double s0 = 0.0, s1 = 0.0;
   uint32_t b = 0;
@@ -1231,13 +1260,13 @@ __device__ __forceinline__ double p1_pairs64(int rc, uint32_t col_s, const ColDe
   for (; r + 2 <= rc; r += 2, b += 2 * c.w) {
     uint32_t c0, c1;
     code_pair<WIDE>(col_s, b, c.w, c0, c1);
-    s0 = fma(vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
-    s1 = fma(vm1_f64(c1, c), signed_f64(c1, c, xr[(r + 1) * xs]), s1);
+    s0 = fma(MID ? vm1_f64_mid(c0, c) : vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
+    s1 = fma(MID ? vm1_f64_mid(c1, c) : vm1_f64(c1, c), signed_f64(c1, c, xr[(r + 1) * xs]), s1);
   }
   if (r < rc) {
     uint32_t c0, c1;
     code_pair<WIDE>(col_s, b, c.w, c0, c1);
-    s0 = fma(vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
+    s0 = fma(MID ? vm1_f64_mid(c0, c) : vm1_f64(c0, c), signed_f64(c0, c, xr[r * xs]), s0);
   }
   return s0 + s1;
 }
@@ -1278,6 +1307,8 @@ __device__ bool consume_phase1_f64(const DevLayout &L, uint32_t np, uint32_t &it
       const double *xr = aux + sg.xs + sub;
       if (c.fast32) {
         dot = narrow ? p1_pairs64<false>(rc, smem_u32(col), c, xr, int(G)) : p1_pairs64<true>(rc, smem_u32(col), c, xr, int(G));
+      } else if (c.mid32 && c.w <= 31) {  // mantissas wider than FP32's: exact v - 1 by integer ops
+        dot = p1_pairs64<true, true>(rc, smem_u32(col), c, xr, int(G));
       } else {
         uint32_t bit = 0;
         for (int r = 0; r < rc; ++r, bit += c.w) dot = fma(dec_f64(bc_code64(col, bit), c), xr[r * int(G)], dot);
