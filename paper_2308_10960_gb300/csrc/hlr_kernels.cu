@@ -1136,7 +1136,7 @@ __device__ __forceinline__ double signed_f64(uint32_t code, const ColDec &c, dou
 // Phase 2, FP64 accumulation, AFL codes: one lane per column slice of the leaf, FP64 row sums
 // in registers (one multiply-add per value), a butterfly over the warp and the four warps'
 // sums into ysum at the end of the leaf (as consume_phase2_pairs).
-template <bool WIDE, bool MID = false>
+template <bool WIDE>
 __device__ __forceinline__ void p2_pairs64(double (&acc)[64], int nr, uint32_t col_s, const ColDec &c, double mult) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -1148,10 +1148,8 @@ __device__ __forceinline__ void p2_pairs64(double (&acc)[64], int nr, uint32_t c
       if (!whole && 2 * p >= nr) break;
       uint32_t c0, c1;
       code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
-      const double v0 = MID ? vm1_f64_mid(c0, c) : vm1_f64(c0, c);
-      const double v1 = MID ? vm1_f64_mid(c1, c) : vm1_f64(c1, c);
-      acc[2 * p] = fma(v0, signed_f64(c0, c, mult), acc[2 * p]);
-      acc[2 * p + 1] = fma(v1, signed_f64(c1, c, mult), acc[2 * p + 1]);
+      acc[2 * p] = fma(vm1_f64(c0, c), signed_f64(c0, c, mult), acc[2 * p]);
+      acc[2 * p + 1] = fma(vm1_f64(c1, c), signed_f64(c1, c, mult), acc[2 * p + 1]);
     }
   }
 }
@@ -1210,9 +1208,6 @@ __device__ bool consume_phase2_f64(const DevLayout &L, uint32_t np, uint32_t &it
       if (active) p2_pairs64<false>(acc, nr, smem_u32(col), c, mult);
     } else if (__all_sync(kFull, !active || c.fast32)) {
       if (active) p2_pairs64<true>(acc, nr, smem_u32(col), c, mult);
-    } else if (__all_sync(kFull, !active || (c.mid32 && c.w <= 31))) {
-      // mantissas wider than FP32's: the exact v - 1 from integer operations, two codes per window
-      if (active) p2_pairs64<true, true>(acc, nr, smem_u32(col), c, mult);
     } else if (active) {
       p2_rows64(acc, nr, col, c, mult);
     }
