@@ -7,25 +7,31 @@
 //               a block wider than 256 rows is split into items whose partial sums are
 //               written to scratch and summed in chunk order by k_combine
 //   k_combine : deterministic sum of those partial sums, times the column factor
-//   k_product<FMT, 1> (phase 2): per leaf row interval l (<= 64 rows), y|l += the sum over the
-//               blocks covering l of W~_b|l t_b and D~_b|l x|sigma in one fixed order; the one
-//               CTA that owns the leaf reads each row of y when the leaf starts and writes
-//               y + (row total) when it ends: no atomics on y, a deterministic result
+//   k_product<FMT, 1> (phase 2): per leaf row interval l (<= 64 rows), the sum over the blocks
+//               covering l of W~_b|l t_b and D~_b|l x|sigma in one fixed order, by the one CTA
+//               that owns the leaf; the AFL paths write it as a row total in cluster order and
+//   k_scatter : y[perm[p]] += total[p] (the other formats add into y at the leaf's end): no
+//               atomics on y, a deterministic result
+//   multi-column passes (R = 8 or 32 right-hand sides): the same two phases with R dot
+//               products per value (phase 1) and a tensor-core contraction (phase 2)
 //
 // Both phases are persistent kernels over the work-ordered piece streams (hlr_internal.h):
 // one producer warp per CTA issues TMA bulk copies (cp.async.bulk) of the next pieces and of
-// their multipliers into a ring of shared-memory slots guarded by mbarriers. In the consumer
-// warps of the compressed paths every lane owns one column slice of the current piece (phase 1:
-// a <= 64-row part of an X column; phase 2: a column of the leaf). Phase 2 in FP32 writes the
-// lanes' products of 16 rows to a padded tile per warp and sums it transposed; the FP64 paths
-// let lanes be rows instead (one FP64 fused multiply-add per value, no cross-lane sums).
-// Every wait is bounded (about 2 s of clock cycles), after which the kernel records an error
-// word and returns.
+// their multipliers into a ring of shared-memory slots guarded by mbarriers; every lane of a
+// consumer warp fences its reads against the async proxy before the warp hands a slot back. In
+// the consumer warps of the compressed paths every lane owns one column slice of the current
+// piece (phase 1: a <= 64-row part of an X column; phase 2: a column of the leaf). Phase 2 keeps
+// 64 row sums per lane in registers over the leaf's pieces and reduces them over the warp with a
+// butterfly at the leaf's end; the FP64 route of the plain FP64 format lets lanes be rows. Every
+// wait is bounded (about 2 s of clock cycles), after which the kernel records an error word and
+// returns.
 //
-// FMT_AFL32: codes -> FP32 bit patterns with integer ops; FP32 sums over a slice (phase 1) or
-//            over the <= 32 slices of a warp (phase 2); compensated FP32 pairs across pieces;
-//            FP64 for the final per-row sum into y.
-// FMT_AFL64: codes -> FP64, FP64 sums.   FMT_RAW64: plain FP64 factors (uncompressed baseline).
+// FMT_AFL32: codes -> FP32 bit patterns with integer ops (two codes per 32- or 64-bit window);
+//            FP32 sums over a slice (phase 1) or over a lane's slices of a leaf and the warp's
+//            lanes (phase 2); FP64 over the four warps and into y.
+// FMT_AFL64: codes -> FP64 (one FP64 fused multiply-add per value), FP64 sums.
+// FMT_RAW64: plain FP64 factors (uncompressed baseline). FMT_BFL32 / DFL32 / MP32: the
+//            byte-aligned and mixed-precision formats with FP32 accumulation.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
