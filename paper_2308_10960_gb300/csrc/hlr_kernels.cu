@@ -987,7 +987,7 @@ __device__ bool consume_phase2_reg(const DevLayout &L, uint32_t np, uint32_t &it
 // row sum that is never stored.
 static_assert(8 * 128 <= kSlotPad + kAuxMax2 * 4, "phase-2 window reads stay inside the slot");
 
-template <bool WIDE, bool MID = false>
+template <bool WIDE>
 __device__ __forceinline__ void p2_pairs(float (&acc)[64], int nr, uint32_t col_s, const ColDec &c, float mult) {
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
@@ -999,13 +999,8 @@ __device__ __forceinline__ void p2_pairs(float (&acc)[64], int nr, uint32_t col_
       if (!whole && 2 * p >= nr) break;
       uint32_t c0, c1;
       code_pair<WIDE>(col_s, uint32_t(2 * p) * c.w, c.w, c0, c1);
-      if constexpr (MID) {  // the products p2_rows<1> forms
-        acc[2 * p] += dec_mid32(c0, c) * mult;
-        acc[2 * p + 1] += dec_mid32(c1, c) * mult;
-      } else {
-        acc[2 * p] += dec_mul_f32(c0, c, mult);
-        acc[2 * p + 1] += dec_mul_f32(c1, c, mult);
-      }
+      acc[2 * p] += dec_mul_f32(c0, c, mult);
+      acc[2 * p + 1] += dec_mul_f32(c1, c, mult);
     }
   }
 }
@@ -1058,11 +1053,8 @@ __device__ bool consume_phase2_pairs(const DevLayout &L, uint32_t np, uint32_t &
     } else {
       // mantissas wider than FP32's: the FP64 route's values from FP32 operations
       const bool mid = __all_sync(kFull, !active || c.mid32);
-      const bool midp = mid && __all_sync(kFull, !active || c.w <= 31);
       if (active) {
-        if (midp)
-          p2_pairs<true, true>(acc, nr, smem_u32(col), c, mult);  // two codes per window
-        else if (mid)
+        if (mid)
           p2_rows<1, FMT>(acc, nr, col, c, mult);
         else
           p2_rows<2, FMT>(acc, nr, col, c, mult);
