@@ -37,7 +37,7 @@ extern "C" {
 #define HLR_ERR_CUDA        (-3)  /* a CUDA runtime call or kernel launch failed             */
 #define HLR_ERR_TIMEOUT     (-4)  /* a bounded device-side wait expired                      */
 #define HLR_ERR_NOCONV      (-5)  /* CG reached maxit; x holds the last iterate              */
-#define HLR_ERR_UNSUPPORTED (-6)  /* valid request outside this build's limits               */
+#define HLR_ERR_UNSUPPORTED (-6)  /* valid request outside this library's limits             */
 
 /* ---- block kinds and storage formats ---------------------------------------------------- */
 #define HLR_DENSE   0
