@@ -73,10 +73,13 @@ template <>
 struct Tr<FMT_MP32> : Tr<FMT_AFL32> {};
 constexpr int kRB = 32;         // right-hand sides per pass of the multi-RHS product (widest pass)
 constexpr int kRN = 8;          // width of the narrow pass, for requests of at most 8 columns
-// row stride (floats) of a warp's multipliers in a multi-RHS phase 2: a multiple of 8 that is 8
-// modulo 32, so that the B fragment loads (rows tq, columns g) hit 32 different banks
+// B-fragment column swizzle of a warp's multipliers in a multi-RHS phase 2 (rows of R floats):
+// with R = 32, row k keeps column n at n ^ 8 (k % 4), so that the fragment loads (rows 8 kg + tq
+// and + 4, columns 8 nt + g) hit 32 different banks; with R = 8 the plain layout already does
 template <int R>
-constexpr int kMS = R % 32 == 8 ? R : R + 8;
+__host__ __device__ constexpr int kSwz(int k) {
+  return R == 32 ? (k & 3) << 3 : 0;
+}
 constexpr int kMaxBatch = 64;   // products per launch of the batched path
 
 // One product of a launch. Single right-hand side (R = 1): y += A~ x with the handle's scratch.
@@ -110,10 +113,10 @@ __host__ __device__ constexpr size_t slot_bytes() {
   return size_t(kPieceMax) + kSlotPad + (R == 1 ? size_t(PH == 0 ? kAuxMax1 : kAuxMax2) * Tr<FMT>::esz : 0);
 }
 // phase-2 tiles of one warp: 16 rows x 33 (single RHS, accumulation type) or, for a multi-RHS
-// pass, a 16 x 36 decode tile and the 32 slices' R multipliers (floats)
+// pass, a 16 x 36 decode tile and the 32 slices' R multipliers split into TF32 hi and lo parts
 template <int FMT, int R>
 __host__ __device__ constexpr size_t tile_bytes() {
-  return R > 1 ? (size_t(16) * 36 + 32 * kMS<R>) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
+  return R > 1 ? (size_t(16) * 36 + 2 * 32 * R) * 4 : FMT == FMT_RAW64 ? 0 : size_t(16) * 33 * Tr<FMT>::esz;
 }
 // dynamic shared memory: ring, mbarriers; phase 2 adds the leaf reduction buffers (single RHS:
 // two halves; multi-RHS: the tiles, and in the same space, once a leaf is done, each warp's
@@ -1826,9 +1829,10 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
   const int g = lane >> 2, tq = lane & 3;  // mma fragment coordinates
   const float4 *xp4 = reinterpret_cast<const float4 *>(jb.xp);
   const float4 *tw4 = reinterpret_cast<const float4 *>(jb.tw);
-  constexpr int MS = kMS<R>;
-  float *tile = tiles + warp * (16 * kTS + 32 * MS);
-  float *mbuf = tile + 16 * kTS;                              // [32 slices][MS] multipliers of the warp
+  float *tile = tiles + warp * (16 * kTS + 2 * 32 * R);
+  uint32_t *mhi = reinterpret_cast<uint32_t *>(tile + 16 * kTS);  // [32 slices][R] TF32 hi parts (swizzled)
+  uint32_t *mlo = mhi + 32 * R;                                    // [32 slices][R] TF32 lo parts
+  const int swz = kSwz<R>(tq);  // this lane's B rows are 8 kg + tq and 8 kg + tq + 4
   float *red = tiles;  // [kCWarps][64 rows][R + 8] leaf sums, over the tiles once every warp is done
   float c[4][R / 8][4];  // per 16-row tile and 8-column tile: C fragment (rows g, g + 8; columns 2 tq, 2 tq + 1)
 #pragma unroll
@@ -1858,34 +1862,44 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
 #pragma unroll
           for (int e = 0; e < 4; ++e) c[a][b][e] = 0.f;
     }
-    // the lane's slice and its R multipliers (zero for idle lanes)
+    // the lane's slice and its R multipliers (zero for idle lanes), split once into the TF32
+    // parts the B fragments take
     LaneHdr hd{0xff, 0, 0, 0};
     const uint32_t *col = Wd;
     bool active = false;
-    float4 *mrow = reinterpret_cast<float4 *>(mbuf + lane * MS);
+    const Seg *sgp = nullptr;
     if (t < int(ph->ncols)) {
       const LaneHdr h = lane_hdrs(sl, ph)[t];
       if (h.seg != 0xff) {
-        const Seg &sg = segs[h.seg];
-        if (sg.kind == SEG_DENSE) {
-          const float mm = float(sg.m_min);
-#pragma unroll
-          for (int q = 0; q < R / 4; ++q) {
-            const float4 xv = __ldg(xp4 + (size_t(sg.gx) + h.j) * (R / 4) + q);
-            mrow[q] = make_float4(xv.x * mm, xv.y * mm, xv.z * mm, xv.w * mm);
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < R / 4; ++q) mrow[q] = __ldg(tw4 + (size_t(sg.gx) + h.j) * (R / 4) + q);
-        }
+        sgp = &segs[h.seg];
         hd = h;
         col = Wd + bc_column(ph, t);
         active = true;
       }
     }
-    if (!active) {
+    {
+      const int rs = kSwz<R>(lane);  // this lane writes row `lane` of the multipliers
 #pragma unroll
-      for (int q = 0; q < R / 4; ++q) mrow[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int q = 0; q < R / 4; ++q) {
+        float4 mv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active) {
+          if (sgp->kind == SEG_DENSE) {
+            const float mm = float(sgp->m_min);
+            const float4 xv = __ldg(xp4 + (size_t(sgp->gx) + hd.j) * (R / 4) + q);
+            mv = make_float4(xv.x * mm, xv.y * mm, xv.z * mm, xv.w * mm);
+          } else {
+            mv = __ldg(tw4 + (size_t(sgp->gx) + hd.j) * (R / 4) + q);
+          }
+        }
+        uint4 hi, lo;
+        tf32_split(mv.x, hi.x, lo.x);
+        tf32_split(mv.y, hi.y, lo.y);
+        tf32_split(mv.z, hi.z, lo.z);
+        tf32_split(mv.w, hi.w, lo.w);
+        const int cidx = lane * R + ((4 * q) ^ rs);
+        *reinterpret_cast<uint4 *>(mhi + cidx) = hi;
+        *reinterpret_cast<uint4 *>(mlo + cidx) = lo;
+      }
     }
     const ColDec cd = lane_dec(hd);
     const bool fast = __all_sync(kFull, !active || cd.fast32);
@@ -1924,10 +1938,8 @@ __device__ bool consume_phase2_multi_mma(const Job &jb, uint32_t np, uint32_t &i
 #pragma unroll
         for (int nt = 0; nt < R / 8; ++nt) {
           // B[k][n] = multiplier n of slice 8 kg + k, columns 8 nt .. 8 nt + 7
-          const float b0 = mbuf[(8 * kg + tq) * MS + 8 * nt + g], b1 = mbuf[(8 * kg + tq + 4) * MS + 8 * nt + g];
-          const uint32_t bh0 = tf32_of(b0), bh1 = tf32_of(b1);
-          const uint32_t bl0 = tf32_of(b0 - __uint_as_float(bh0)), bl1 = tf32_of(b1 - __uint_as_float(bh1));
-          mma3_add(c[mt][nt], ah, al, bh0, bh1, bl0, bl1);
+          const int i0 = (8 * kg + tq) * R + ((8 * nt + g) ^ swz), i1 = i0 + 4 * R;
+          mma3_add(c[mt][nt], ah, al, mhi[i0], mhi[i1], mlo[i0], mlo[i1]);
         }
       }
       __syncwarp();  // the tile is rewritten for the next rows
