@@ -179,10 +179,11 @@ int hlr_matvec_host(hlr_handle h, const double *x_host, double *y_host, int flag
  * products each (permute, phase 1, combine, phase 2 per launch group; the job list is a kernel
  * parameter, so no device memory is allocated per call and the call can be captured in a CUDA
  * graph once the scratch below exists). With HLR_ACC_FP32, requests with several columns
- * run in passes of up to 32 columns that decode each value once (phase 2 on the tensor cores;
- * phase 1 on the tensor cores for a wide pass, with FP32 fused multiply-adds for a pass of at
- * most 8 columns); their pass scratch is allocated per handle on first use and grown when a
- * request needs more passes. HLR_MULTI instead runs every column as its own product (see
+ * run in passes of up to 32 columns that decode each value once (phase 2 on the tensor cores,
+ * phase 1 with FP32 fused multiply-adds; a pass of more than 8 columns stages the decoded values
+ * in shared memory so that the columns of a block share each x row); their pass scratch is
+ * allocated per handle on first use and grown when a request needs more passes.
+ * HLR_MULTI instead runs every column as its own product (see
  * there) on per-column scratch sets, allocated one by one on first use and kept until
  * hlr_free. Call once with the widest requests before capturing.
  * FP64 accumulation and plain FP64 storage run one product per column.

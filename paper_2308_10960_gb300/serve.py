@@ -5,18 +5,18 @@ solves against several matrices kept resident on one GPU.
   HBM budget next to the resident ones; otherwise idle resident matrices are evicted, least
   recently used first. A request waits while its matrix cannot be admitted.
 * Batching: whenever the GPU finishes a batch, all queued products of every resident idle matrix
-  (up to ``max_rhs`` per matrix) go into ONE ``hlr_matvec_batched`` call, several requests of a
-  matrix becoming the columns of a multi-right-hand-side product. With ``HLR_MULTI`` a column's
-  result does not depend on what it is batched with, so a request gets the same bits alone and
-  in the mix.
+  (up to ``max_rhs`` per matrix) go into ONE ``hlr_matvec_batched`` call. With ``HLR_MULTI``
+  every column is a product of its own (many per launch) on a scratch set of its own, so a
+  request gets the bits of ``matvec`` alone and in the mix, and a batch never shares scratch
+  with a solve of the same matrix.
 * Solves: unpreconditioned CG (``hlr_solve_cg``) runs in worker threads on their own streams,
   overlapping the product batches; the library call releases the interpreter lock. Its
   product kernels take a share of the CTA slots (``HLR_SM_SHARE``, half by default) and it
   reads its residual from the host only every few iterations, so product batches find room on
   the SMs while solves run.
 * A matrix runs at most one product batch and at most one solve at a time: the batches use the
-  multi-RHS pass scratch of its handle, the solves the single-RHS scratch and the CG workspace,
-  so one of each may overlap.
+  per-column scratch sets of its handle, the solves the handle's own scratch and the CG
+  workspace, so one of each may overlap.
 
 Latency = finish - arrival per request; the run reports p50/p99 per request kind, throughput
 and the algorithmic bytes moved. The backend is pluggable: ``GpuBackend`` drives the library,
